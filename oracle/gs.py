@@ -52,15 +52,19 @@ def amplitude_constraint(R, Ts):
     return Ts * np.exp(1j * ang)
 
 
-def initial_field(target, table, L, seed, start=0, levels=256, init_phase=None):
-    """E_0 = T_s * exp(i*theta): LUT phases drawn for s = 0, or a caller-given phase."""
+def initial_field(target, table, L, seed, start=0, lut_levels=256, init_phase=None):
+    """E_0 = T_s * exp(i*theta): LUT phases drawn for s = 0, or a caller-given phase.
+
+    The table holds phase codes of ``lut_levels`` levels (8-bit codes, Section 5.2); they
+    are independent of the levels the hologram is quantised to.
+    """
     Ts = energy_scaled_target(target)
     H, W = Ts.shape
     if init_phase is not None:
         theta = np.asarray(init_phase, dtype=np.float64).reshape(H, W)
     else:
-        c = _lut.subframe_codes(table, L, seed, start, 0, H * W, H * W, levels)
-        theta = _lut.phase_of_codes(c, levels).reshape(H, W)
+        c = _lut.subframe_codes(table, L, seed, start, 0, H * W, H * W, lut_levels)
+        theta = _lut.phase_of_codes(c, lut_levels).reshape(H, W)
     return Ts * np.exp(1j * theta)
 
 
@@ -74,13 +78,17 @@ def gs_step(E, Ts, levels=256):
     return q, R, eps, amplitude_constraint(R, Ts)
 
 
-def gs(target, iters, table, L, seed, start=0, levels=256, init_phase=None, init_field=None):
-    """K iterations. Returns (q [H,W] int64, I = |R|^2 [H,W], eps [K], E_state [H,W])."""
+def gs(target, iters, table, L, seed, start=0, levels=256, init_phase=None, init_field=None,
+       lut_levels=256):
+    """K iterations. Returns (q [H,W] int64, I = |R|^2 [H,W], eps [K], E_state [H,W]).
+
+    ``levels`` is the hologram's phase quantisation; ``lut_levels`` the table codes' levels.
+    """
     Ts = energy_scaled_target(target)
     if init_field is not None:
         E = np.asarray(init_field, dtype=np.complex128)
     else:
-        E = initial_field(target, table, L, seed, start, levels, init_phase)
+        E = initial_field(target, table, L, seed, start, lut_levels, init_phase)
     errs = []
     q = R = None
     for _ in range(iters):

@@ -95,6 +95,17 @@ def test_first_iteration_by_hand():
     assert np.max(np.abs(E1 - Ts * np.exp(1j * np.angle(R)))) < 1e-12
 
 
+def test_lut_levels_independent_of_hologram_levels():
+    # the initial phase comes from 8-bit table codes whatever the hologram's levels are
+    H = W = 32
+    T = blob_target(H, W, 1012)
+    table = lut.lut_codes(6, 101)
+    E256 = gs.initial_field(T, table, 101, 6)
+    q2, _, e2, _ = gs.gs(T, 1, table, 101, 6, levels=2)
+    q2b, _, e2b, _ = gs.gs(T, 1, None, 0, 0, levels=2, init_field=E256)
+    assert np.array_equal(q2, q2b) and np.allclose(e2, e2b, rtol=1e-14)
+
+
 def test_caller_phase_start_equals_lut_phase():
     H = W = 16
     T = blob_target(H, W, 1008)
