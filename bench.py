@@ -1,0 +1,421 @@
+"""Benchmark: OSPR 1024x1024 binary sub-frames/s (and GS iterations/s) on GB300.
+
+Workload (one "step"): the L sweep of the 1024x1024 binary OSPR case, N = 24 sub-frames
+per frame, one frame for each table length L in 2^8 .. 2^20 plus the unrepeated
+generator (14 frames, 336 sub-frames), alternating seeded blob and band-limited-noise
+targets. Each frame runs the whole hot path through the C ABI: lut_build ->
+ospr_generate (LUT-apply, back-propagation IDFT, binarise, replay DFT, accumulate) ->
+replay_error. GS (1024x1024, 20 iterations, 256 levels, LUT-random start, L = 10007)
+is timed in the same run and reported beside it.
+
+Timing: W warm-up steps, then K steps each bracketed by CUDA events on the launching
+stream; L2 is flushed (a 512 MiB write) before every timed step, outside the events.
+The dominant kernel's duration comes from the library's own CUDA-event profiling of
+every launch in the timed steps. `--impl reference` times the float64 CPU oracle on
+the host cores instead (a bounded sample of the same workload).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 1024
+N_SF = 24
+L_SWEEP = [1 << k for k in range(8, 21)] + [-1]          # 2^8 .. 2^20, unrepeated
+LUT_SEED = 7
+GS_ITERS = 20
+GS_L = 10007
+FLUSH_BYTES = 512 << 20
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def _query_once(self):
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                 timeout=10).stdout
+            self._parse(out)
+        except (OSError, subprocess.SubprocessError):
+            pass
+
+    def _parse(self, text):
+        for line in text.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def start(self):
+        self._query_once()
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.buf = []
+            self.th = threading.Thread(target=lambda: self.buf.extend(self.proc.stdout), daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
+            self._parse("".join(self.buf))
+        self._query_once()
+        return self.summary()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[3:]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ byte models ----
+def kernel_bytes(family, P, pairs, groups, N):
+    """Algorithmic HBM bytes of one launch (unique bytes the kernel must read and write)."""
+    if family == "ospr_row":
+        return pairs * (16 * P + 2 * P // 8)
+    if family == "ospr_col_ifft":
+        return 4 * P + pairs * 8 * P + min(2 * pairs * P, 1 << 20)
+    if family == "ospr_col_fft":
+        return pairs * 8 * P + groups * 4 * P
+    if family == "ospr_finalize":
+        return groups * 4 * P + 4 * P
+    if family in ("err_pass1", "err_pass2"):
+        return 8 * P
+    if family == "lut_build":
+        return 0
+    return None
+
+
+def subframe_bytes(P, N, L):
+    """Section 8(d) model of one OSPR sub-frame: 16 B/px of transform round trips, the bits,
+    and the per-frame target, accumulator and table bytes shared by the N sub-frames."""
+    lut = min(L if L > 0 else 0, N * P)
+    return 16 * P + P // 8 + (4 * P + 8 * P + lut) / N
+
+
+# ------------------------------------------------------------------ our arm ----
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2004_04049_gb300 import holo, pipeline
+    from synthetic import blob_target, noise_target
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    holo.load()
+    P = H * W
+    stream = torch.cuda.current_stream(dev)
+
+    targets = [torch.from_numpy(blob_target(H, W, 1000 + rank)).to(dev),
+               torch.from_numpy(noise_target(H, W, 2000 + rank)).to(dev)]
+    maxL = max(L_SWEEP)
+    codes = torch.empty(maxL, dtype=torch.uint8, device=dev)
+    ws = torch.empty(holo.ospr_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
+    ews = torch.empty(holo.replay_error_workspace_size(H, W), dtype=torch.uint8, device=dev)
+    bits = torch.empty((N_SF, P // 32), dtype=torch.int32, device=dev)
+    replay = torch.empty((H, W), dtype=torch.float32, device=dev)
+    errs = torch.empty((len(L_SWEEP), 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def frame(i, L, tgt):
+        if L > 0:
+            holo.lut_build(LUT_SEED, L, 256, codes, None, stream=stream.cuda_stream)
+        pipeline.ospr(tgt, N_SF, codes if L > 0 else None, L, 256, LUT_SEED, 0, 0,
+                      ws=ws, out_bits=bits, out_replay=replay, stream=stream.cuda_stream)
+        pipeline.error(replay, tgt, ws=ews, out=errs[i], stream=stream.cuda_stream)
+
+    def step():
+        for i, L in enumerate(L_SWEEP):
+            frame(i, L, targets[i % 2])
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    holo.holo_profile_reset()
+    launches0 = holo.holo_launch_count()
+    sampler = ClockSampler(local)
+    sampler.start()
+    holo.holo_profile_enable(True)
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        times.append((e0, e1))
+    barrier()
+    holo.holo_profile_enable(False)
+    clocks = sampler.stop()
+    launches = holo.holo_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in times]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    subframes_per_step = len(L_SWEEP) * N_SF
+    value = world * subframes_per_step * args.steps / (total_ms / 1e3)
+
+    # per-kernel durations from the library's event timing over the timed steps
+    fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "err_pass1",
+            "err_pass2"]
+    prof = {f: holo.holo_profile_read(f) for f in fams}
+    npairs = (N_SF + 1) // 2
+    groups = min(npairs, 4)
+    dom = max(fams, key=lambda f: prof[f][1])
+    n_dom, ms_dom = prof[dom]
+    peaks = _peaks()
+    peak_bw = peaks["hbm_gbs"] if peaks else 6800.0
+    bytes_dom = kernel_bytes(dom, P, npairs, groups, N_SF)
+    achieved = bytes_dom / (ms_dom / n_dom / 1e3) / 1e9 if n_dom and bytes_dom else None
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
+                "frac": achieved / peak_bw if achieved else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": bytes_dom,
+                "avg_launch_us": ms_dom / n_dom * 1e3 if n_dom else None,
+                "kernel_share": {f: round(prof[f][1] / max(1e-12, sum(v[1] for v in prof.values())), 4)
+                                 for f in fams}}
+    sf_bytes = np.mean([subframe_bytes(P, N_SF, L if L > 0 else N_SF * P) for L in L_SWEEP])
+    path_gbs = value / world * sf_bytes / 1e9
+
+    # GS leg: 1024^2, 20 iterations, LUT-random start
+    gcodes = torch.empty(GS_L, dtype=torch.uint8, device=dev)
+    holo.lut_build(LUT_SEED, GS_L, 256, gcodes, None, stream=stream.cuda_stream)
+    gws = torch.empty(holo.gs_workspace_size(H, W, GS_ITERS), dtype=torch.uint8, device=dev)
+    gq = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    gI = torch.empty((H, W), dtype=torch.float32, device=dev)
+    gerr = torch.empty(GS_ITERS, dtype=torch.float64, device=dev)
+    gout = torch.empty(3, dtype=torch.float64, device=dev)
+
+    def gs_run():
+        holo.gs_iterate(targets[0], H, W, GS_ITERS, 256, None, gcodes, GS_L, 256, LUT_SEED, 0, 0,
+                        gq, gI, gerr, None, None, gws, gws.numel(), stream=stream.cuda_stream)
+
+    for _ in range(3):
+        gs_run()
+    barrier()
+    gs_runs = max(3, args.steps)
+    gs_ms = 0.0
+    for _ in range(gs_runs):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gs_run()
+        e1.record(stream)
+        e1.synchronize()
+        gs_ms += e0.elapsed_time(e1)
+    pipeline.error(gI, targets[0], out=gout, stream=stream.cuda_stream)
+    gs_nmse = float(gout[2].item())
+    gs_ips = GS_ITERS * gs_runs / (gs_ms / 1e3)
+
+    # end to end through the public API: host target in, bits + replay + error out
+    h_targets = [t.cpu().pin_memory() for t in targets]
+    h_bits = torch.empty((N_SF, P // 32), dtype=torch.int32).pin_memory()
+    h_replay = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    h_err = torch.empty(3, dtype=torch.float64).pin_memory()
+    d_tgt = torch.empty((H, W), dtype=torch.float32, device=dev)
+    e2e_steps = max(1, min(args.steps, 10))
+
+    def e2e_step():
+        for i, L in enumerate(L_SWEEP):
+            d_tgt.copy_(h_targets[i % 2], non_blocking=True)
+            frame(i, L, d_tgt)
+            h_bits.copy_(bits, non_blocking=True)
+            h_replay.copy_(replay, non_blocking=True)
+            h_err.copy_(errs[i], non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e2e_ms = 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_value = world * subframes_per_step * e2e_steps / (e2e_ms / 1e3)
+    nmse = errs[:, 2].cpu().numpy()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(seconds=args.cpu_seconds)
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": "OSPR 1024x1024 binary sub-frames/s (L sweep 2^8..2^20 + unrepeated, N=24)",
+            "value": value, "unit": "sub-frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ospr_1024x1024_N24_Lsweep", "H": H, "W": W, "N": N_SF,
+                       "L": "2^8..2^20 + unrepeated", "frames_per_step": len(L_SWEEP),
+                       "targets": "seeded blob / band-limited noise", "l2": "flushed before each step",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "path_bytes_model": {"bytes_per_subframe": sf_bytes, "achieved_GBps": path_gbs,
+                                 "frac_of_hbm": path_gbs / peak_bw},
+            "gs": {"metric": "GS 1024x1024 iterations/s (20 iterations, 256 levels, L=10007)",
+                   "value": gs_ips, "unit": "iter/s", "nmse_after_20": gs_nmse,
+                   "bytes_per_iter_model": 36 * P,
+                   "achieved_GBps": gs_ips * 36 * P / 1e9},
+            "nmse_per_L": {str(L): float(v) for L, v in zip(L_SWEEP, nmse)},
+            "e2e": {"value": e2e_value, "unit": "sub-frames/s",
+                    "h2d_bytes_per_step": len(L_SWEEP) * 4 * P,
+                    "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 4 * P + 24)},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- CPU oracle arm ----
+def _oracle_subframes(n_sub, L=1 << 16):
+    """Runs n_sub sub-frames of the workload's 1024x1024 frame through the oracle."""
+    from oracle import error as oerr
+    from oracle import lut as olut
+    from oracle import ospr as oospr
+    from synthetic import blob_target
+
+    T = blob_target(H, W, 1000)
+    table = olut.lut_codes(LUT_SEED, L)
+    P = H * W
+    I = np.zeros((H, W))
+    for s in range(n_sub):
+        c = olut.subframe_codes(table, L, LUT_SEED, 0, s, P, P)
+        Hs = oospr.back_propagate(oospr.subframe_field(T, c))
+        h = oospr.binarise(Hs.real)
+        oospr.pack_bits(h)
+        I += oospr.replay_intensity(h)
+    oerr.replay_error(I / n_sub, T)
+
+
+def cpu_baseline_sample(seconds=15.0):
+    """The oracle as it stands on the host cores: sub-frames of the 1024x1024 workload."""
+    t0 = time.perf_counter()
+    _oracle_subframes(1)
+    one = time.perf_counter() - t0
+    n = max(1, int(seconds / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    _oracle_subframes(n)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "sub-frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} sub-frames of the 1024x1024 L=65536 frame (float64 numpy oracle, "
+                      f"one thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    per_step = 2
+    for _ in range(args.warmup):
+        _oracle_subframes(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_subframes(per_step)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference",
+        "metric": "OSPR 1024x1024 binary sub-frames/s (L sweep 2^8..2^20 + unrepeated, N=24)",
+        "value": value, "unit": "sub-frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ospr_1024x1024_N24_Lsweep", "H": H, "W": W, "N": N_SF,
+                   "sample_per_step": f"{per_step} sub-frames"},
+        "cpu_baseline": {"value": value, "unit": "sub-frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} sub-frames of the 1024x1024 frame per step"},
+        "e2e": {"value": value, "unit": "sub-frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

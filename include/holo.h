@@ -1,0 +1,214 @@
+/*
+ * holo.h - C ABI of the GB300 library for LUT phase randomisation, One-Step
+ * Phase-Retrieval (OSPR) and Gerchberg-Saxton (GS) hologram generation
+ * (arXiv 2004.04049, "Lookup tables for phase randomisation in hardware generated
+ * holograms").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Images are row-major float32 [H][W]; pixel p = r*W + c (column index fastest).
+ *    H and W are powers of two in [64, 4096] unless a call says otherwise.
+ *  - Every pointer named d_* is a device pointer on the current CUDA device. The caller
+ *    owns all of them (inputs, outputs and the workspace) and keeps them alive until the
+ *    stream has finished the call. The library never frees caller memory.
+ *  - Every call is asynchronous on the caller's stream `s` (NULL = the legacy default
+ *    stream). The return value reports argument validation and launch errors only;
+ *    errors raised while the kernels run surface at the next synchronisation and via
+ *    holo_check().
+ *  - Return codes: HOLO_OK (0) or a negative holo_status. A message for the last
+ *    non-OK return (and for design-rule warnings returned with HOLO_OK) is available
+ *    from holo_last_error() on the same host thread.
+ *  - There is no CPU fallback: without a usable CUDA device every compute call fails
+ *    with HOLO_ECUDA.
+ *  - Transforms are the unitary DFT of Eq. 1 (forward, exp(-2 pi i ...)) and Eq. 2
+ *    (inverse, exp(+2 pi i ...)), scale 1/sqrt(H*W).
+ */
+#ifndef HOLO_H
+#define HOLO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so this header needs no CUDA headers. */
+typedef struct CUstream_st* holo_stream_t;
+
+typedef enum holo_status {
+    HOLO_OK = 0,
+    HOLO_EINVAL = -1,        /* a pointer, size or count is invalid */
+    HOLO_EUNSUPPORTED = -2,  /* a valid value this build does not implement */
+    HOLO_ECUDA = -3,         /* a CUDA runtime call failed (no device, launch error) */
+    HOLO_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
+    HOLO_ENOMEM = -5,        /* the library could not allocate its own small state */
+    HOLO_EWORKSPACE = -6     /* the caller's workspace is missing or too small */
+} holo_status;
+
+typedef enum holo_precision {
+    HOLO_FP32 = 0,     /* all transforms in float32 */
+    HOLO_FP16X2 = 1,   /* DFT-32 stages on tensor cores, fp16 hi+lo operands, fp32 accumulate */
+    HOLO_BF16X2 = 2    /* DFT-32 stages on tensor cores, bf16 hi+lo operands, fp32 accumulate */
+} holo_precision;
+
+/* L value selecting the per-pixel generator with no table (the "unrepeated" case). */
+#define HOLO_L_UNREPEATED (-1)
+
+/* ---------------------------------------------------------------- utilities ---- */
+
+/* Library version, major*10000 + minor*100 + patch. */
+int holo_version(void);
+
+/* Message of the last non-OK return on this host thread (or of a warning returned with
+ * HOLO_OK); "" if none. The pointer stays valid until the next call on this thread. */
+const char* holo_last_error(void);
+
+/* Synchronises stream s and reports any CUDA error raised by earlier calls, and the
+ * library's sticky device status (HOLO_ETIMEOUT if a bounded wait gave up). */
+int holo_check(holo_stream_t s);
+
+/* Number of kernels this library has launched in this process (all devices). */
+int holo_launch_count(uint64_t* out_count);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around every
+ * launch while enabled. holo_profile_read synchronises the recorded events and returns,
+ * for the kernel family `name`, the number of launches and their summed duration in
+ * milliseconds since the last holo_profile_reset. Families: "lut_build",
+ * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "gs_prepare",
+ * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2". */
+int holo_profile_enable(int on);
+int holo_profile_reset(void);
+int holo_profile_read(const char* name, uint64_t* launches, double* total_ms);
+
+/* ------------------------------------------------------------- phase LUT ---- */
+
+/*
+ * lut_build - fill the phase lookup table ("pool") of Section 4: L random phase codes
+ * generated once and then drawn sequentially (Section 5, Fig. 3). The entries are
+ * 8-bit codes (Section 5.2: "over 12 Mb" for 256x256x24 entries).
+ *
+ *   seed     generator stream; entry k holds the top log2(levels) bits of the k-th
+ *            SplitMix64 output, mix(seed + (k+1)*0x9E3779B97F4A7C15).
+ *   L        number of entries, 1 <= L <= 2^31 - 1.
+ *   levels   phase levels, a power of two in [2, 256]; code c means 2*pi*c/levels.
+ *   d_codes  [L] uint8 output.
+ *   d_cs     [2L] float32 output (cos, sin of each entry's phase, interleaved), or NULL.
+ * Errors: HOLO_EINVAL for L out of range, bad levels or NULL d_codes.
+ */
+int lut_build(uint64_t seed, int64_t L, int levels, uint8_t* d_codes, float* d_cs,
+              holo_stream_t s);
+
+/* ------------------------------------------------------------------- OSPR ---- */
+
+/*
+ * ospr_workspace_size - bytes of device workspace ospr_generate needs for this shape.
+ */
+int ospr_workspace_size(int H, int W, int N, int precision, size_t* bytes);
+
+/*
+ * ospr_generate - N binary-phase OSPR sub-frames of one target and their time-averaged
+ * replay (Section 2: back-propagate, quantise; Section 3: random phase per sub-frame;
+ * Section 5.2 / Section 6: binary phase device).
+ *
+ * Per sub-frame s in [0, N):
+ *   draw index of pixel p   i = start_index + s*stride + p     (Fig. 3 continuation)
+ *   code                    c = d_codes[i mod L]               (L > 0)
+ *                           c = top bits of SplitMix64(seed, i) (L == HOLO_L_UNREPEATED)
+ *                           c = 0                               (L == 0: flat phase)
+ *   E = T * exp(2*pi*i*c/levels);  H_s = IDFT(E) (Eq. 2)
+ *   h_s = +1 where Re H_s >= 0, else -1
+ *   I  += |DFT(h_s)|^2 / N  (Eq. 1)
+ *
+ *   d_target     [H][W] float32 target amplitude (>= 0).
+ *   N            sub-frames, 1 <= N <= 4096.
+ *   d_codes      [L] uint8 codes (ignored, may be NULL, when L <= 0).
+ *   L            table length (>= 0) or HOLO_L_UNREPEATED.
+ *   levels       code levels, power of two in [2, 256] (the table's levels).
+ *   seed         generator stream for L == HOLO_L_UNREPEATED (ignored otherwise).
+ *   start_index  draw index of pixel 0 of sub-frame 0 (>= 0): frames that share one
+ *                table continue from the previous frame's end (Fig. 3).
+ *   subframe_stride  draw-index step between sub-frames; 0 means H*W.
+ *   precision    HOLO_FP32 (the tensor-core modes return HOLO_EUNSUPPORTED until built).
+ *   d_holo_bits  [N][H*W/32] uint32 output or NULL: bit j of word w is pixel 32*w + j
+ *                of that sub-frame, 1 for -1.
+ *   d_replay     [H][W] float32 output or NULL: mean replay intensity over sub-frames.
+ *   d_ws         device workspace of at least ospr_workspace_size() bytes, 256-byte
+ *                aligned.
+ * Design-rule warnings (Section 8: L prime, L > N, L > max(H, W)) are returned with
+ * HOLO_OK and a message in holo_last_error(). Errors: HOLO_EINVAL, HOLO_EUNSUPPORTED,
+ * HOLO_EWORKSPACE, HOLO_ECUDA.
+ */
+int ospr_generate(const float* d_target, int H, int W, int N,
+                  const uint8_t* d_codes, int64_t L, int levels, uint64_t seed,
+                  int64_t start_index, int64_t subframe_stride, int precision,
+                  uint32_t* d_holo_bits, float* d_replay,
+                  void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/* --------------------------------------------------------------------- GS ---- */
+
+/*
+ * gs_workspace_size - bytes of device workspace gs_iterate needs.
+ */
+int gs_workspace_size(int H, int W, int iters, int precision, size_t* bytes);
+
+/*
+ * gs_iterate - Gerchberg-Saxton iterations with a phase-quantised hologram (Section 2;
+ * random initial phase of Section 3 drawn from the LUT; Section 8: for GS only the
+ * prime-length and longer-than-the-largest-dimension rules apply).
+ *
+ * T_s = T * sqrt(H*W / sum T^2). Start field E (replay plane): d_state_in if given,
+ * else T_s * exp(i*phi) with phi = d_init_phase if given, else the LUT phases of
+ * sub-frame 0 (draw index start_index + p, same code rules as ospr_generate).
+ * Iteration k = 1..iters:
+ *   H = IDFT(E); q = floor(levels*arg(H)/(2 pi) + 1/2) mod levels (arg(0) = 0);
+ *   h = exp(2 pi i q/levels); R = DFT(h); eps_k = sum (|R| - T_s)^2;
+ *   E = T_s * exp(i arg R)  (arg(0) = 0)
+ *
+ *   levels        hologram phase levels, a power of two in [2, 256] (2 = binary).
+ *   d_init_phase  [H][W] float32 radians or NULL.
+ *   d_codes, L, lut_levels, seed, start_index: the initial-phase LUT (as ospr_generate).
+ *   d_phase_codes [H][W] uint8 output or NULL: q of the last iteration.
+ *   d_replay      [H][W] float32 output or NULL: |R|^2 of the last iteration.
+ *   d_err         [iters] float64 output or NULL: eps_k.
+ *   d_state_in    [H][W][2] float32 (re, im) replay-plane field to resume from, or NULL.
+ *   d_state_out   [H][W][2] float32 output or NULL: E after the last iteration.
+ * Errors: HOLO_EINVAL, HOLO_EUNSUPPORTED, HOLO_EWORKSPACE, HOLO_ECUDA.
+ */
+int gs_iterate(const float* d_target, int H, int W, int iters, int levels,
+               const float* d_init_phase,
+               const uint8_t* d_codes, int64_t L, int lut_levels, uint64_t seed,
+               int64_t start_index, int precision,
+               uint8_t* d_phase_codes, float* d_replay, double* d_err,
+               const float* d_state_in, float* d_state_out,
+               void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/* ------------------------------------------------------------ replay error ---- */
+
+/*
+ * replay_error_workspace_size - bytes of device workspace replay_error needs.
+ */
+int replay_error_workspace_size(int H, int W, size_t* bytes);
+
+/*
+ * replay_error - error of a replay intensity against its target (Section 5.2, Eq. 3),
+ * with the intensity-domain, optimal-scale reading:
+ *   alpha = sum(I*T^2) / sum(I^2);  mse = sum((alpha*I - T^2)^2) / P;
+ *   nmse  = sum((alpha*I - T^2)^2) / sum(T^4)
+ * All sums in float64, two passes, fixed reduction order (bit-reproducible).
+ *
+ *   d_replay  [H][W] float32 intensity I.   d_target [H][W] float32 amplitude T.
+ *   d_mask    [H][W] uint8 or NULL: nonzero pixels are included (P = their count).
+ *   H, W      any sizes with 1 <= H*W <= 2^28 (not restricted to powers of two).
+ *   d_out     [3] float64 output: alpha, mse, nmse.
+ * Errors: HOLO_EINVAL, HOLO_EWORKSPACE, HOLO_ECUDA.
+ */
+int replay_error(const float* d_replay, const float* d_target, const uint8_t* d_mask,
+                 int H, int W, double* d_out, void* d_ws, size_t ws_bytes,
+                 holo_stream_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOLO_H */

@@ -1,0 +1,407 @@
+// gs.cu - Gerchberg-Saxton with a phase-quantised hologram (paper Section 2; random
+// initial phase of Section 3 drawn from the LUT; Section 8's GS design rules).
+//
+// Replay-plane field E, target scaled to the hologram's energy T_s = T*sqrt(P/sum T^2).
+// Iteration: H = IDFT(E); q = quantise(arg H); h = exp(2 pi i q/levels); R = DFT(h);
+// eps = sum (|R| - T_s)^2; E = T_s exp(i arg R).
+//
+// Passes (one global round trip of the complex field each; the field stays resident):
+//   prepare    sum T^2 -> scale (float64 grid reduction)
+//   col_init   columns: E_0 from the LUT / a phase / a saved state, column IDFT
+//   row        rows: row IDFT, quantise (codes out on the last iteration), row DFT
+//   col        columns: column DFT, error partials, amplitude constraint, column IDFT
+//              (the next iteration's first half); on the last iteration it writes
+//              |R|^2 and the state instead of transforming back
+//   finish     per-iteration float64 error sums
+#include <cmath>
+
+#include "fft_core.cuh"
+#include "phase_source.cuh"
+#include "reduce.cuh"
+#include "runtime.h"
+
+namespace holo {
+
+// column passes: small column tiles so that a single field fills the GPU
+template <int N> struct GsColCfg;
+template <> struct GsColCfg<64>   { static constexpr int R = 8,  LPC = 8; };
+template <> struct GsColCfg<128>  { static constexpr int R = 16, LPC = 8; };
+template <> struct GsColCfg<256>  { static constexpr int R = 16, LPC = 8; };
+template <> struct GsColCfg<512>  { static constexpr int R = 16, LPC = 4; };
+template <> struct GsColCfg<1024> { static constexpr int R = 16, LPC = 4; };
+template <> struct GsColCfg<2048> { static constexpr int R = 32, LPC = 4; };
+template <> struct GsColCfg<4096> { static constexpr int R = 32, LPC = 2; };
+template <int N> struct GsRowCfg;
+template <> struct GsRowCfg<64>   { static constexpr int R = 2,  LPR = 4; };
+template <> struct GsRowCfg<128>  { static constexpr int R = 4,  LPR = 4; };
+template <> struct GsRowCfg<256>  { static constexpr int R = 8,  LPR = 4; };
+template <> struct GsRowCfg<512>  { static constexpr int R = 16, LPR = 4; };
+template <> struct GsRowCfg<1024> { static constexpr int R = 32, LPR = 4; };
+template <> struct GsRowCfg<2048> { static constexpr int R = 32, LPR = 2; };
+template <> struct GsRowCfg<4096> { static constexpr int R = 32, LPR = 1; };
+
+constexpr int kGsPrepThreads = 256;
+constexpr int kGsPrepBlocks = 152;
+
+struct GsScalars {
+    unsigned int ticket;
+    unsigned int pad[63];
+    double sum_t2;
+    float scale;        // sqrt(P / sum T^2)
+    float pad2[61];
+};
+
+struct GsArgs {
+    const float* target;
+    int H, W, levels_bits;
+    PhaseSource ps;              // initial phase from the LUT
+    const float* init_phase;     // or a caller phase
+    const float2* state_in;      // or a saved field
+    float2* y;                   // [H][W] complex work field
+    GsScalars* sc;
+    double* err_part;            // [iters][col blocks]
+    int iter;
+    uint8_t* codes_out;
+    float* replay_out;
+    float2* state_out;
+    const float2* tw;
+    const float2* cs256;
+    float inv_sqrt_p;
+};
+
+template <int NC>
+constexpr size_t gs_col_smem() {
+    return sizeof(float2) * (256 + size_t(GsColCfg<NC>::LPC) * line_stride(NC, GsColCfg<NC>::R));
+}
+template <int NR>
+constexpr size_t gs_row_smem() {
+    return sizeof(float2) * (256 + size_t(GsRowCfg<NR>::LPR) * line_stride(NR, GsRowCfg<NR>::R));
+}
+
+// ----------------------------------------------------------------- prepare ----
+__global__ void __launch_bounds__(kGsPrepThreads)
+k_gs_prepare(const float* __restrict__ T, int64_t P, GsScalars* sc, double* partials) {
+    __shared__ double sm[32];
+    __shared__ int s_last;
+    float acc = 0.f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P; i += int64_t(gridDim.x) * blockDim.x)
+        acc = fmaf(T[i], T[i], acc);
+    const double b = block_sum(double(acc), sm);
+    if (!grid_partial_done(b, partials, &sc->ticket, &s_last)) return;
+    const double tot = sum_partials(partials, gridDim.x, sm);
+    if (threadIdx.x == 0) {
+        sc->sum_t2 = tot;
+        sc->scale = tot > 0.0 ? float(sqrt(double(P) / tot)) : 0.f;
+    }
+}
+
+// --------------------------------------------------------------- col_init ----
+template <int NC>
+__global__ void __launch_bounds__((NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC)
+k_gs_col_init(GsArgs a) {
+    constexpr int R = GsColCfg<NC>::R, LPC = GsColCfg<NC>::LPC, T = NC / R;
+    extern __shared__ float2 sm[];
+    float2* cs = sm;
+    float2* lines = sm + 256;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) cs[i] = a.cs256[i];
+    __syncthreads();
+    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
+    const int W = a.W;
+    const int c = blockIdx.x * LPC + lc;
+    const float scale = a.sc->scale;
+    const SubframeDraw d0 = subframe_draw(a.ps, 0);
+    float2 v[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const uint32_t p = uint32_t(t + T * e) * uint32_t(W) + uint32_t(c);
+        if (a.state_in) {
+            v[e] = a.state_in[p];
+        } else {
+            const float ts = __ldg(a.target + p) * scale;
+            float2 ph;
+            if (a.init_phase) sincosf(__ldg(a.init_phase + p), &ph.y, &ph.x);
+            else ph = cs[draw_code(a.ps, d0, p) << a.ps.cs_shift];
+            v[e] = make_float2(ts * ph.x, ts * ph.y);
+        }
+    }
+    line_fft<NC, R, +1, true>(v, lines + lc * line_stride(NC, R), t, a.tw);
+#pragma unroll
+    for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
+}
+
+// -------------------------------------------------------------------- row ----
+template <int NR>
+__global__ void __launch_bounds__((NR / GsRowCfg<NR>::R) * GsRowCfg<NR>::LPR)
+k_gs_row(GsArgs a) {
+    constexpr int R = GsRowCfg<NR>::R, T = NR / R;
+    constexpr bool BLOCK = T > 32;
+    extern __shared__ float2 sm[];
+    float2* cs = sm;
+    float2* lines = sm + 256;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) cs[i] = a.cs256[i];
+    __syncthreads();
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const int r = blockIdx.x * GsRowCfg<NR>::LPR + line;
+    float2* z = a.y + size_t(r) * NR;
+    float2* buf = lines + line * line_stride(NR, R);
+    float2 v[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
+    line_fft<NR, R, +1, BLOCK>(v, buf, t, a.tw);
+    const int levels = 1 << a.levels_bits;
+    const float k_code = float(levels) * 0.15915494309189533577f;   // levels / (2 pi)
+    const int shift = 8 - a.levels_bits;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const float ang = atan2f(v[e].y, v[e].x);
+        const int q = int(floorf(fmaf(ang, k_code, 0.5f))) & (levels - 1);
+        if (a.codes_out) a.codes_out[size_t(r) * NR + t + T * e] = uint8_t(q);
+        v[e] = cs[q << shift];
+    }
+    line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
+#pragma unroll
+    for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
+}
+
+// -------------------------------------------------------------------- col ----
+template <int NC, bool LAST>
+__global__ void __launch_bounds__((NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC)
+k_gs_col(GsArgs a) {
+    constexpr int R = GsColCfg<NC>::R, LPC = GsColCfg<NC>::LPC, T = NC / R;
+    extern __shared__ float2 sm[];
+    __shared__ double red[32];
+    float2* lines = sm + 256;
+    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
+    const int W = a.W;
+    const int c = blockIdx.x * LPC + lc;
+    float2* buf = lines + lc * line_stride(NC, R);
+    float2 v[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) v[e] = a.y[size_t(t + T * e) * W + c];
+    line_fft<NC, R, -1, true>(v, buf, t, a.tw);
+    const float scale = a.sc->scale;
+    float err = 0.f;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const size_t p = size_t(t + T * e) * W + c;
+        const float2 Rv = make_float2(v[e].x * a.inv_sqrt_p, v[e].y * a.inv_sqrt_p);
+        const float amp = sqrtf(fmaf(Rv.x, Rv.x, Rv.y * Rv.y));
+        const float ts = __ldg(a.target + p) * scale;
+        const float d = amp - ts;
+        err = fmaf(d, d, err);
+        float2 En = make_float2(ts, 0.f);
+        if (amp > 0.f) {
+            const float f = ts / amp;
+            En = make_float2(Rv.x * f, Rv.y * f);
+        }
+        if constexpr (LAST) {
+            if (a.replay_out) a.replay_out[p] = amp * amp;
+            if (a.state_out) a.state_out[p] = En;
+        }
+        v[e] = En;
+    }
+    const double b = block_sum(double(err), red);
+    if (threadIdx.x == 0) a.err_part[size_t(a.iter) * gridDim.x + blockIdx.x] = b;
+    if constexpr (!LAST) {
+        line_fft<NC, R, +1, true>(v, buf, t, a.tw);
+#pragma unroll
+        for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
+    }
+}
+
+// ----------------------------------------------------------------- finish ----
+__global__ void k_gs_finish(const double* __restrict__ err_part, int nb, double* __restrict__ err) {
+    __shared__ double sm[32];
+    const double v = sum_partials(err_part + size_t(blockIdx.x) * nb, nb, sm);
+    if (threadIdx.x == 0) err[blockIdx.x] = v;
+}
+
+// ------------------------------------------------------------------- host ----
+template <int NC>
+static int launch_col_init(const GsArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = gs_col_smem<NC>();
+    int rc = ensure_smem((const void*)k_gs_col_init<NC>, smem, &mask);
+    if (rc) return rc;
+    Launch ln("gs_col_init", st);
+    k_gs_col_init<NC><<<a.W / GsColCfg<NC>::LPC, (NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC, smem, st>>>(a);
+    return ln.done("gs_col_init launch");
+}
+template <int NR>
+static int launch_row(const GsArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = gs_row_smem<NR>();
+    int rc = ensure_smem((const void*)k_gs_row<NR>, smem, &mask);
+    if (rc) return rc;
+    Launch ln("gs_row", st);
+    k_gs_row<NR><<<a.H / GsRowCfg<NR>::LPR, (NR / GsRowCfg<NR>::R) * GsRowCfg<NR>::LPR, smem, st>>>(a);
+    return ln.done("gs_row launch");
+}
+template <int NC>
+static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
+    static uint64_t mask0 = 0, mask1 = 0;
+    constexpr size_t smem = gs_col_smem<NC>();
+    const int grid = a.W / GsColCfg<NC>::LPC, threads = (NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC;
+    int rc = last ? ensure_smem((const void*)k_gs_col<NC, true>, smem, &mask1)
+                  : ensure_smem((const void*)k_gs_col<NC, false>, smem, &mask0);
+    if (rc) return rc;
+    Launch ln("gs_col", st);
+    if (last) k_gs_col<NC, true><<<grid, threads, smem, st>>>(a);
+    else k_gs_col<NC, false><<<grid, threads, smem, st>>>(a);
+    return ln.done("gs_col launch");
+}
+
+#define HOLO_GS_SWITCH(n, CALL)                           \
+    switch (n) {                                          \
+        case 64: return CALL(64);                         \
+        case 128: return CALL(128);                       \
+        case 256: return CALL(256);                       \
+        case 512: return CALL(512);                       \
+        case 1024: return CALL(1024);                     \
+        case 2048: return CALL(2048);                     \
+        case 4096: return CALL(4096);                     \
+        default: return fail(HOLO_EUNSUPPORTED, "line length %d", n); \
+    }
+
+static int run_col_init(const GsArgs& a, cudaStream_t st) {
+#define C(n) launch_col_init<n>(a, st)
+    HOLO_GS_SWITCH(a.H, C)
+#undef C
+}
+static int run_row(const GsArgs& a, cudaStream_t st) {
+#define C(n) launch_row<n>(a, st)
+    HOLO_GS_SWITCH(a.W, C)
+#undef C
+}
+static int run_col(const GsArgs& a, bool last, cudaStream_t st) {
+#define C(n) launch_col<n>(a, last, st)
+    HOLO_GS_SWITCH(a.H, C)
+#undef C
+}
+static int col_blocks(int H, int W) {
+    switch (H) {
+        case 64: return W / GsColCfg<64>::LPC;
+        case 128: return W / GsColCfg<128>::LPC;
+        case 256: return W / GsColCfg<256>::LPC;
+        case 512: return W / GsColCfg<512>::LPC;
+        case 1024: return W / GsColCfg<1024>::LPC;
+        case 2048: return W / GsColCfg<2048>::LPC;
+        default: return W / GsColCfg<4096>::LPC;
+    }
+}
+
+struct GsLayout {
+    size_t y_off, sc_off, prep_off, err_off, total;
+};
+static GsLayout gs_layout(int H, int W, int iters) {
+    GsLayout l;
+    const size_t P = size_t(H) * W;
+    l.y_off = 0;
+    l.sc_off = align_up(P * sizeof(float2), 256);
+    l.prep_off = l.sc_off + align_up(sizeof(GsScalars), 256);
+    l.err_off = l.prep_off + align_up(sizeof(double) * kGsPrepBlocks, 256);
+    l.total = l.err_off + align_up(sizeof(double) * size_t(iters) * size_t(col_blocks(H, W)), 256);
+    return l;
+}
+
+static int gs_check_shape(const char* who, int H, int W) {
+    if (!is_pow2(H) || !is_pow2(W) || H < kMinDim || W < kMinDim || H > kMaxDim || W > kMaxDim)
+        return fail(HOLO_EUNSUPPORTED, "%s: H=%d W=%d must be powers of two in [%d, %d]", who, H, W,
+                    kMinDim, kMaxDim);
+    return HOLO_OK;
+}
+
+}  // namespace holo
+
+using namespace holo;
+
+extern "C" int gs_workspace_size(int H, int W, int iters, int precision, size_t* bytes) {
+    clear_error();
+    if (!bytes) return fail(HOLO_EINVAL, "gs_workspace_size: NULL output");
+    int rc = gs_check_shape("gs_workspace_size", H, W);
+    if (rc) return rc;
+    if (iters < 1 || iters > 100000) return fail(HOLO_EINVAL, "gs_workspace_size: iters=%d", iters);
+    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "gs_workspace_size: precision %d", precision);
+    *bytes = gs_layout(H, W, iters).total;
+    return HOLO_OK;
+}
+
+extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int levels,
+                          const float* d_init_phase,
+                          const uint8_t* d_codes, int64_t L, int lut_levels, uint64_t seed,
+                          int64_t start_index, int precision,
+                          uint8_t* d_phase_codes, float* d_replay, double* d_err,
+                          const float* d_state_in, float* d_state_out,
+                          void* d_ws, size_t ws_bytes, holo_stream_t s) {
+    clear_error();
+    const char* who = "gs_iterate";
+    int rc = gs_check_shape(who, H, W);
+    if (rc) return rc;
+    if (iters < 1 || iters > 100000) return fail(HOLO_EINVAL, "%s: iters=%d out of [1, 100000]", who, iters);
+    if (!is_pow2(levels) || levels < 2 || levels > 256)
+        return fail(HOLO_EINVAL, "%s: levels=%d is not a power of two in [2, 256]", who, levels);
+    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "%s: precision %d is not built", who, precision);
+    if (!d_target) return fail(HOLO_EINVAL, "%s: d_target is NULL", who);
+    PhaseSource ps;
+    const bool use_lut = !d_init_phase && !d_state_in;
+    rc = make_phase_source(who, use_lut ? d_codes : nullptr, use_lut ? L : 0, lut_levels, seed,
+                           start_index, int64_t(H) * W, &ps);
+    if (rc) return rc;
+    const GsLayout lay = gs_layout(H, W, iters);
+    if (!d_ws || ws_bytes < lay.total)
+        return fail(HOLO_EWORKSPACE, "%s: workspace %zu bytes, need %zu", who, ws_bytes, lay.total);
+    if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0)
+        return fail(HOLO_EWORKSPACE, "%s: workspace is not 256-byte aligned", who);
+    Tables tab;
+    rc = device_tables(&tab);
+    if (rc) return rc;
+    char* ws = static_cast<char*>(d_ws);
+    GsArgs a;
+    a.target = d_target;
+    a.H = H;
+    a.W = W;
+    a.levels_bits = log2i(levels);
+    a.ps = ps;
+    a.init_phase = d_init_phase;
+    a.state_in = reinterpret_cast<const float2*>(d_state_in);
+    a.y = reinterpret_cast<float2*>(ws + lay.y_off);
+    a.sc = reinterpret_cast<GsScalars*>(ws + lay.sc_off);
+    a.err_part = reinterpret_cast<double*>(ws + lay.err_off);
+    a.iter = 0;
+    a.codes_out = nullptr;
+    a.replay_out = d_replay;
+    a.state_out = reinterpret_cast<float2*>(d_state_out);
+    a.tw = tab.twiddles;
+    a.cs256 = tab.cs256;
+    a.inv_sqrt_p = float(1.0 / std::sqrt(double(H) * double(W)));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+
+    rc = cuda_status(cudaMemsetAsync(&a.sc->ticket, 0, sizeof(unsigned int), st), "gs_iterate: reset");
+    if (rc) return rc;
+    {
+        Launch ln("gs_prepare", st);
+        k_gs_prepare<<<kGsPrepBlocks, kGsPrepThreads, 0, st>>>(d_target, int64_t(H) * W, a.sc,
+                                                               reinterpret_cast<double*>(ws + lay.prep_off));
+        if ((rc = ln.done("gs_prepare launch"))) return rc;
+    }
+    if ((rc = run_col_init(a, st))) return rc;
+    for (int k = 0; k < iters; ++k) {
+        const bool last = k == iters - 1;
+        a.iter = k;
+        a.codes_out = last ? d_phase_codes : nullptr;
+        if ((rc = run_row(a, st))) return rc;
+        if ((rc = run_col(a, last, st))) return rc;
+    }
+    if (d_err) {
+        Launch ln("gs_finish", st);
+        k_gs_finish<<<iters, 256, 0, st>>>(a.err_part, col_blocks(H, W), d_err);
+        if ((rc = ln.done("gs_finish launch"))) return rc;
+    }
+    if (use_lut && L > 0) {
+        bool prime = L >= 2;
+        for (int64_t d = 2; prime && d * d <= L; ++d) prime = (L % d) != 0;
+        if (!prime) warn("design rule: L=%lld is not prime", (long long)L);
+        if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
+    }
+    return HOLO_OK;
+}

@@ -1,0 +1,238 @@
+// runtime.cu - status, launch accounting, event profiling and device tables.
+#include "runtime.h"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fft_core.cuh"
+
+namespace holo {
+
+// ------------------------------------------------------------------ status ----
+static thread_local std::string t_last_error;
+
+static void vrecord(const char* fmt, va_list ap) {
+    char buf[1024];
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    t_last_error = buf;
+}
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vrecord(fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void warn(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    char buf[1024];
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (!t_last_error.empty()) t_last_error += "; ";
+    t_last_error += buf;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+int cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return HOLO_OK;
+    return fail(HOLO_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------- launches/profiling ----
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_profiling{0};
+
+struct PendingPair {
+    cudaEvent_t start, stop;
+};
+struct FamilyStats {
+    uint64_t launches = 0;
+    double total_ms = 0.0;
+    std::vector<PendingPair> pending;
+};
+static std::mutex g_prof_mu;
+static std::map<std::string, FamilyStats> g_prof;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t take_event() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+Launch::Launch(const char* family, cudaStream_t stream) : family_(family), stream_(stream) {
+    if (g_profiling.load(std::memory_order_relaxed)) {
+        start_ = take_event();
+        if (start_ && cudaEventRecord(start_, stream_) != cudaSuccess) start_ = nullptr;
+    }
+}
+
+int Launch::done(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, what);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (start_) {
+        cudaEvent_t stop = take_event();
+        if (stop && cudaEventRecord(stop, stream_) == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            g_prof[family_].pending.push_back({start_, stop});
+        }
+    }
+    return HOLO_OK;
+}
+
+static int collect_locked() {
+    for (auto& kv : g_prof) {
+        FamilyStats& fs = kv.second;
+        for (auto& pp : fs.pending) {
+            cudaError_t e = cudaEventSynchronize(pp.stop);
+            if (e != cudaSuccess) return cuda_status(e, "profile: cudaEventSynchronize");
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, pp.start, pp.stop);
+            if (e != cudaSuccess) return cuda_status(e, "profile: cudaEventElapsedTime");
+            fs.launches += 1;
+            fs.total_ms += ms;
+            g_event_pool.push_back(pp.start);
+            g_event_pool.push_back(pp.stop);
+        }
+        fs.pending.clear();
+    }
+    return HOLO_OK;
+}
+
+// ---------------------------------------------------------- device tables ----
+static __device__ float2 g_twiddles[kTwiddleTotal];
+static __device__ float2 g_cs256[256];
+
+static std::mutex g_tab_mu;
+static const int kMaxDevices = 64;
+static Tables g_tables[kMaxDevices];
+static bool g_tables_ready[kMaxDevices];
+
+static void host_twiddles(std::vector<float2>& out) {
+    out.assign(kTwiddleTotal, make_float2(0.f, 0.f));
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int lg = kMinLog2; lg <= kMaxLog2; ++lg)
+        for (int lr = 1; lr <= 5; ++lr) {
+            const int N = 1 << lg, R = 1 << lr;
+            for (int s = 1; s < stage_count(N, R); ++s) {
+                const int Ns = stage_ns(N, R, s), Rs = stage_radix(N, R, s);
+                const int off = stage_offset(N, R, s);
+                for (int m = 0; m < Rs; ++m)
+                    for (int k = 0; k < Ns; ++k) {
+                        const double ang = two_pi * double(k) * double(m) / double(Ns * Rs);
+                        out[off + m * Ns + k] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+                    }
+            }
+        }
+}
+
+int device_tables(Tables* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(HOLO_EUNSUPPORTED, "device index %d too large", dev);
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (!g_tables_ready[dev]) {
+        std::vector<float2> tw;
+        host_twiddles(tw);
+        std::vector<float2> cs(256);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int c = 0; c < 256; ++c)
+            cs[c] = make_float2(float(std::cos(two_pi * c / 256.0)), float(std::sin(two_pi * c / 256.0)));
+        e = cudaMemcpyToSymbol(g_twiddles, tw.data(), sizeof(float2) * tw.size());
+        if (e != cudaSuccess) return cuda_status(e, "upload twiddles");
+        e = cudaMemcpyToSymbol(g_cs256, cs.data(), sizeof(float2) * 256);
+        if (e != cudaSuccess) return cuda_status(e, "upload cos/sin table");
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_twiddles);
+        if (e != cudaSuccess) return cuda_status(e, "twiddle address");
+        g_tables[dev].twiddles = static_cast<const float2*>(p);
+        e = cudaGetSymbolAddress(&p, g_cs256);
+        if (e != cudaSuccess) return cuda_status(e, "cos/sin table address");
+        g_tables[dev].cs256 = static_cast<const float2*>(p);
+        g_tables_ready[dev] = true;
+    }
+    *out = g_tables[dev];
+    return HOLO_OK;
+}
+
+int ensure_smem(const void* fn, size_t bytes, uint64_t* device_mask) {
+    if (bytes <= 48 * 1024) return HOLO_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    const uint64_t bit = 1ull << (dev & 63);
+    if (__atomic_load_n(device_mask, __ATOMIC_ACQUIRE) & bit) return HOLO_OK;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(shared memory)");
+    __atomic_fetch_or(device_mask, bit, __ATOMIC_ACQ_REL);
+    return HOLO_OK;
+}
+
+}  // namespace holo
+
+// ================================================================== C ABI ====
+using namespace holo;
+
+extern "C" int holo_version(void) { return 10000; }
+
+extern "C" const char* holo_last_error(void) { return t_last_error.c_str(); }
+
+extern "C" int holo_check(holo_stream_t s) {
+    clear_error();
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s));
+    if (e != cudaSuccess) return cuda_status(e, "holo_check: stream");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "holo_check");
+    return HOLO_OK;
+}
+
+extern "C" int holo_launch_count(uint64_t* out_count) {
+    if (!out_count) return fail(HOLO_EINVAL, "holo_launch_count: NULL output");
+    *out_count = g_launches.load();
+    return HOLO_OK;
+}
+
+extern "C" int holo_profile_enable(int on) {
+    g_profiling.store(on ? 1 : 0);
+    return HOLO_OK;
+}
+
+extern "C" int holo_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int rc = collect_locked();
+    for (auto& kv : g_prof) {
+        kv.second.launches = 0;
+        kv.second.total_ms = 0.0;
+    }
+    return rc;
+}
+
+extern "C" int holo_profile_read(const char* name, uint64_t* launches, double* total_ms) {
+    if (!name || !launches || !total_ms) return fail(HOLO_EINVAL, "holo_profile_read: NULL argument");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int rc = collect_locked();
+    if (rc != HOLO_OK) return rc;
+    auto it = g_prof.find(name);
+    *launches = it == g_prof.end() ? 0 : it->second.launches;
+    *total_ms = it == g_prof.end() ? 0.0 : it->second.total_ms;
+    return HOLO_OK;
+}

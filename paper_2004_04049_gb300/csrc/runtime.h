@@ -1,0 +1,55 @@
+// runtime.h - host-side runtime shared by the library's translation units: status and
+// last-error reporting, kernel-launch accounting, per-kernel CUDA-event timing and the
+// per-device constant tables (FFT twiddles, phase cos/sin).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "holo.h"
+
+namespace holo {
+
+// ---- status -----------------------------------------------------------------
+// Records a message for holo_last_error() on this thread and returns `code`.
+int fail(int code, const char* fmt, ...);
+// Records a warning message (returned later with HOLO_OK).
+void warn(const char* fmt, ...);
+void clear_error();
+// Maps a CUDA error to HOLO_ECUDA with a message; returns HOLO_OK for cudaSuccess.
+int cuda_status(cudaError_t e, const char* what);
+
+// ---- launches ---------------------------------------------------------------
+// Wraps one kernel launch: counts it and, while profiling is on, records CUDA events
+// around it on `stream`. Construct immediately before the launch and call done() with
+// the launch's cudaGetLastError() right after it.
+class Launch {
+  public:
+    Launch(const char* family, cudaStream_t stream);
+    int done(const char* what);
+  private:
+    const char* family_;
+    cudaStream_t stream_;
+    cudaEvent_t start_ = nullptr;
+};
+
+// ---- constant tables ---------------------------------------------------------
+struct Tables {
+    const float2* twiddles;   // Stockham stage twiddles, see fft_core.cuh
+    const float2* cs256;      // (cos, sin)(2*pi*c/256), c < 256
+};
+// Fills the tables on the current device the first time and returns their addresses.
+int device_tables(Tables* out);
+
+// ---- misc -------------------------------------------------------------------
+inline bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+inline int log2i(int64_t x) { int l = 0; while ((int64_t(1) << l) < x) ++l; return l; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr int kMinDim = 64;
+constexpr int kMaxDim = 4096;
+
+// Sets the dynamic shared-memory limit of kernel `fn` on the current device once.
+int ensure_smem(const void* fn, size_t bytes, uint64_t* device_mask);
+
+}  // namespace holo

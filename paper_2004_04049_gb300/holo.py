@@ -1,0 +1,204 @@
+"""ctypes binding of ``libholo.so`` with the C ABI's names (see include/holo.h).
+
+Argument marshalling only: every buffer argument is a torch CUDA tensor (its
+``data_ptr()`` is passed) or None for NULL, and ``stream`` defaults to PyTorch's current
+stream on the tensor's device. Every step of the computation runs in the library's
+kernels; there is no fallback. A missing library or a non-OK status raises.
+"""
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libholo.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "holo.h")
+
+HOLO_OK = 0
+HOLO_EINVAL = -1
+HOLO_EUNSUPPORTED = -2
+HOLO_ECUDA = -3
+HOLO_ETIMEOUT = -4
+HOLO_ENOMEM = -5
+HOLO_EWORKSPACE = -6
+HOLO_FP32, HOLO_FP16X2, HOLO_BF16X2 = 0, 1, 2
+L_UNREPEATED = -1
+
+_STATUS_NAMES = {0: "HOLO_OK", -1: "HOLO_EINVAL", -2: "HOLO_EUNSUPPORTED", -3: "HOLO_ECUDA",
+                 -4: "HOLO_ETIMEOUT", -5: "HOLO_ENOMEM", -6: "HOLO_EWORKSPACE"}
+
+
+class HoloError(RuntimeError):
+    def __init__(self, status, func, message):
+        super().__init__(f"{func} -> {_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+_c = ctypes
+_SIGS = {
+    "holo_version": (_c.c_int, []),
+    "holo_last_error": (_c.c_char_p, []),
+    "holo_check": (_c.c_int, [_c.c_void_p]),
+    "holo_launch_count": (_c.c_int, [_c.POINTER(_c.c_uint64)]),
+    "holo_profile_enable": (_c.c_int, [_c.c_int]),
+    "holo_profile_reset": (_c.c_int, []),
+    "holo_profile_read": (_c.c_int, [_c.c_char_p, _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_double)]),
+    "lut_build": (_c.c_int, [_c.c_uint64, _c.c_int64, _c.c_int, _c.c_void_p, _c.c_void_p, _c.c_void_p]),
+    "ospr_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "ospr_generate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int,
+                                 _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
+                                 _c.c_int64, _c.c_int64, _c.c_int,
+                                 _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "gs_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "gs_iterate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
+                              _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
+                              _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
+                              _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "replay_error_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "replay_error": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int,
+                                _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+}
+
+
+def load(path=None):
+    """Load libholo.so (once) and return the ctypes handle. Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run paper_2004_04049_gb300.build_lib.build() "
+                           "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions(header=HEADER):
+    """Names of the functions include/holo.h declares."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    dev = None
+    for t in tensors:
+        if t is not None and not isinstance(t, int):
+            dev = t.device
+            break
+    if dev is None:
+        return 0            # raw pointers: the legacy default stream
+    import torch
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _call(name, *args):
+    lib = load()
+    rc = getattr(lib, name)(*args)
+    if rc != HOLO_OK:
+        msg = lib.holo_last_error().decode(errors="replace")
+        raise HoloError(rc, name, msg)
+    return rc
+
+
+def last_error():
+    return load().holo_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------ utilities ----
+def holo_version():
+    return load().holo_version()
+
+
+def holo_check(stream=None):
+    return _call("holo_check", _stream(stream))
+
+
+def holo_launch_count():
+    n = ctypes.c_uint64(0)
+    _call("holo_launch_count", ctypes.byref(n))
+    return n.value
+
+
+def holo_profile_enable(on=True):
+    return _call("holo_profile_enable", 1 if on else 0)
+
+
+def holo_profile_reset():
+    return _call("holo_profile_reset")
+
+
+def holo_profile_read(name):
+    n = ctypes.c_uint64(0)
+    ms = ctypes.c_double(0.0)
+    _call("holo_profile_read", name.encode(), ctypes.byref(n), ctypes.byref(ms))
+    return n.value, ms.value
+
+
+# ------------------------------------------------------------------- compute ----
+def lut_build(seed, L, levels, d_codes, d_cs=None, stream=None):
+    return _call("lut_build", seed, L, levels, _ptr(d_codes), _ptr(d_cs), _stream(stream, d_codes))
+
+
+def ospr_workspace_size(H, W, N, precision=HOLO_FP32):
+    b = ctypes.c_size_t(0)
+    _call("ospr_workspace_size", H, W, N, precision, ctypes.byref(b))
+    return b.value
+
+
+def ospr_generate(d_target, H, W, N, d_codes, L, levels, seed, start_index, subframe_stride,
+                  precision, d_holo_bits, d_replay, d_ws, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("ospr_generate", _ptr(d_target), H, W, N, _ptr(d_codes), L, levels, seed,
+                 start_index, subframe_stride, precision, _ptr(d_holo_bits), _ptr(d_replay),
+                 _ptr(d_ws), ws_bytes, _stream(stream, d_target))
+
+
+def gs_workspace_size(H, W, iters, precision=HOLO_FP32):
+    b = ctypes.c_size_t(0)
+    _call("gs_workspace_size", H, W, iters, precision, ctypes.byref(b))
+    return b.value
+
+
+def gs_iterate(d_target, H, W, iters, levels, d_init_phase, d_codes, L, lut_levels, seed,
+               start_index, precision, d_phase_codes, d_replay, d_err, d_state_in, d_state_out,
+               d_ws, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("gs_iterate", _ptr(d_target), H, W, iters, levels, _ptr(d_init_phase),
+                 _ptr(d_codes), L, lut_levels, seed, start_index, precision,
+                 _ptr(d_phase_codes), _ptr(d_replay), _ptr(d_err), _ptr(d_state_in),
+                 _ptr(d_state_out), _ptr(d_ws), ws_bytes, _stream(stream, d_target))
+
+
+def replay_error_workspace_size(H, W):
+    b = ctypes.c_size_t(0)
+    _call("replay_error_workspace_size", H, W, ctypes.byref(b))
+    return b.value
+
+
+def replay_error(d_replay, d_target, d_mask, H, W, d_out, d_ws, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("replay_error", _ptr(d_replay), _ptr(d_target), _ptr(d_mask), H, W, _ptr(d_out),
+                 _ptr(d_ws), ws_bytes, _stream(stream, d_replay))

@@ -18,3 +18,16 @@ def pytest_configure(config):
 @pytest.fixture
 def golden_dir():
     return GOLDEN
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    """The first CUDA device, with libholo.so built and loaded; fails (no skip) without one."""
+    import torch
+
+    assert torch.cuda.is_available(), "a CUDA GPU is required for -m gpu tests"
+    from paper_2004_04049_gb300 import build_lib, holo
+
+    build_lib.build()
+    holo.load()
+    return torch.device("cuda:0")

@@ -1,0 +1,77 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/holo.h
+declares. Only host-side paths run here (sizes, argument validation): no GPU is needed."""
+
+import ctypes
+
+import pytest
+
+from paper_2004_04049_gb300 import build_lib, holo
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return holo.load()
+
+
+def test_header_declares_the_boundary():
+    names = holo.header_functions()
+    for required in ("lut_build", "ospr_generate", "gs_iterate", "replay_error",
+                     "ospr_workspace_size", "gs_workspace_size", "replay_error_workspace_size",
+                     "holo_last_error", "holo_check"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = holo.header_functions()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding marshals every declared function
+    assert set(names) <= set(holo._SIGS), set(names) - set(holo._SIGS)
+
+
+def test_version_and_empty_error(lib):
+    assert holo.holo_version() >= 10000
+    assert isinstance(holo.last_error(), str)
+
+
+def test_workspace_sizes_are_host_only(lib):
+    a = holo.ospr_workspace_size(1024, 1024, 24)
+    # 12 pairs of complex64 fields in flight plus 4 float32 accumulators
+    assert a >= 12 * 1024 * 1024 * 8 + 4 * 1024 * 1024 * 4
+    assert holo.ospr_workspace_size(256, 256, 1) >= 256 * 256 * 8
+    assert holo.gs_workspace_size(1024, 1024, 20) >= 1024 * 1024 * 8
+    assert holo.replay_error_workspace_size(2, 2) > 0
+
+
+@pytest.mark.parametrize("H,W", [(100, 128), (32, 64), (8192, 64), (64, 0)])
+def test_unsupported_shapes_rejected(lib, H, W):
+    with pytest.raises(holo.HoloError) as ei:
+        holo.ospr_workspace_size(H, W, 4)
+    assert ei.value.status in (holo.HOLO_EUNSUPPORTED, holo.HOLO_EINVAL)
+    assert "H=" in holo.last_error()
+
+
+def test_argument_validation_before_any_cuda_call(lib):
+    # rejected on the host: no device is touched
+    with pytest.raises(holo.HoloError) as ei:
+        holo.lut_build(1, 0, 256, None)
+    assert ei.value.status == holo.HOLO_EINVAL
+    with pytest.raises(holo.HoloError) as ei:
+        holo.lut_build(1, 16, 3, 1 << 20)
+    assert ei.value.status == holo.HOLO_EINVAL
+    rc = lib.ospr_generate(None, 256, 256, 4, None, 0, 256, 0, 0, 0, 0, None, None, None, 0, None)
+    assert rc == holo.HOLO_EINVAL
+    rc = lib.ospr_generate(1 << 20, 256, 256, 4, None, 0, 256, 0, 0, 0, 7, None, 1 << 20, 1 << 20,
+                           1 << 30, None)
+    assert rc == holo.HOLO_EUNSUPPORTED
+    rc = lib.ospr_generate(1 << 20, 256, 256, 4, None, 0, 256, 0, 0, 0, 0, None, 1 << 20, 1 << 20,
+                           16, None)
+    assert rc == holo.HOLO_EWORKSPACE
+    rc = lib.gs_iterate(1 << 20, 256, 256, 0, 256, None, None, 0, 256, 0, 0, 0,
+                        None, None, None, None, None, None, 0, None)
+    assert rc == holo.HOLO_EINVAL
+    rc = lib.replay_error(None, None, None, 4, 4, None, None, 0, None)
+    assert rc == holo.HOLO_EINVAL
+    n = ctypes.c_uint64(0)
+    assert lib.holo_launch_count(ctypes.byref(n)) == 0

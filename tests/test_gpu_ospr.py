@@ -1,0 +1,190 @@
+"""ospr_generate on the GPU against the float64 oracle (Sections 2, 3, 5.1, 5.2, 6).
+
+Element-by-element parity at sizes the oracle finishes in seconds (several FFT tiles,
+odd N for the ragged last pair, every table mode), then the full 1024x1024, N = 24
+workload in the benchmark's launch configuration, checked on sampled outputs.
+Tolerances: tests/parity.py.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import error as oerr
+from oracle import lut as olut
+from oracle import ospr as oospr
+from paper_2004_04049_gb300 import holo, pipeline
+from parity import check_bits, check_nmse, check_replay, unpack
+from synthetic import blob_target, noise_target
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_ospr(cuda, T, N, L, seed, levels=256, start=0, stride=0):
+    t = torch.from_numpy(T).to(cuda)
+    codes = pipeline.lut(seed, L, levels, device=cuda) if L > 0 else None
+    bits, I = pipeline.ospr(t, N, codes, L, levels, seed, start, stride)
+    err = pipeline.error(I, t)
+    torch.cuda.synchronize()
+    return (bits.cpu().numpy().view(np.uint32), I.cpu().numpy(), err.cpu().numpy(),
+            codes.cpu().numpy().astype(np.int64) if codes is not None else None)
+
+
+CASES = [
+    # H, W, N, L, target kind
+    (256, 256, 8, 4096, "blob"),          # the plain FP32 workload: L = 4096 divides H*W
+    (256, 256, 8, 4099, "blob"),          # its prime companion
+    (64, 64, 1, 1031, "blob"),            # a single sub-frame
+    (64, 128, 3, 257, "noise"),           # odd N: last pair holds one sub-frame
+    (128, 64, 5, 10007, "blob"),
+    (512, 256, 4, 65537, "noise"),
+    (128, 128, 6, 0, "blob"),             # flat phase (L = 0)
+    (128, 128, 4, holo.L_UNREPEATED, "blob"),
+    (64, 64, 7, 1, "noise"),              # one entry: every pixel the same phase
+]
+
+
+@pytest.mark.parametrize("H,W,N,L,kind", CASES)
+def test_parity_elementwise(cuda, H, W, N, L, kind):
+    T = blob_target(H, W, 1000) if kind == "blob" else noise_target(H, W, 2000)
+    seed = 7
+    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, N, L, seed)
+    table = olut.lut_codes(seed, L) if L > 0 else None
+    if L > 0:
+        assert np.array_equal(gcodes, table)
+    ob, oI, ex = oospr.ospr(T, N, table, L, seed, keep_fields=True)
+    check_bits(gb, ob, ex["re_h"], H * W)
+    # stage-wise replay: the oracle replays the GPU's bits
+    I_from_bits = oospr.replay_from_bits(gb, H, W)
+    check_replay(gI, I_from_bits)
+    # error: GPU reduction of the GPU replay vs the oracle's error of the same replay
+    o_stage = oerr.replay_error(gI, T)
+    check_nmse(gerr[2], o_stage[2])
+    check_nmse(gerr[1], o_stage[1])
+    # end to end against the oracle's own replay
+    o_e2e = oerr.replay_error(oI, T)
+    check_nmse(gerr[2], o_e2e[2])
+
+
+@pytest.mark.parametrize("levels", [2, 16])
+def test_parity_other_code_levels(cuda, levels):
+    H = W = 128
+    T = blob_target(H, W, 1001)
+    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, 4, 1031, 9, levels=levels)
+    table = olut.lut_codes(9, 1031, levels)
+    assert np.array_equal(gcodes, table)
+    ob, oI, ex = oospr.ospr(T, 4, table, 1031, 9, levels=levels, keep_fields=True)
+    check_bits(gb, ob, ex["re_h"], H * W)
+    check_replay(gI, oospr.replay_from_bits(gb, H, W))
+
+
+def test_start_and_stride(cuda):
+    H, W, N, L = 64, 64, 4, 997
+    T = blob_target(H, W, 1002)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, L, 3, start=12345, stride=777)
+    table = olut.lut_codes(3, L)
+    ob, oI, ex = oospr.ospr(T, N, table, L, 3, start=12345, stride=777, keep_fields=True)
+    check_bits(gb, ob, ex["re_h"], H * W)
+
+
+def test_continuation_between_frames(cuda):
+    # Fig. 3: a frame that starts where the previous frame stopped equals the second half of
+    # one long run
+    H, W, L = 64, 64, 1009
+    T = blob_target(H, W, 1003)
+    P = H * W
+    a, _, _, _ = _gpu_ospr(cuda, T, 6, L, 5)
+    b, _, _, _ = _gpu_ospr(cuda, T, 3, L, 5, start=3 * P)
+    assert np.array_equal(a[3:], b)
+
+
+def test_invariants_on_gpu_outputs(cuda):
+    H, W, N = 256, 512, 6
+    T = noise_target(H, W, 2001)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, 10007, 1)
+    twin = np.roll(np.flip(gI), shift=(1, 1), axis=(0, 1))
+    assert np.array_equal(gI, twin)                    # symmetrised by construction
+    assert abs(gI.sum() / (H * W) - 1.0) < 1e-4        # unitarity: energy P per sub-frame
+
+
+def test_length_dividing_pixels_repeats_subframes(cuda):
+    H = W = 256
+    T = blob_target(H, W, 1004)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, 8, 4096, 7)       # 4096 divides 65536
+    bits = unpack(gb, H * W)
+    for s in range(1, 8):
+        assert np.mean(bits[s] == bits[0]) >= 0.9999
+
+
+def test_long_table_equals_generator_bit_exact(cuda):
+    H = W = 64
+    N = 3
+    T = blob_target(H, W, 1005)
+    a, Ia, _, _ = _gpu_ospr(cuda, T, N, N * H * W, 11)
+    b, Ib, _, _ = _gpu_ospr(cuda, T, N, holo.L_UNREPEATED, 11)
+    assert np.array_equal(a, b)
+    assert np.array_equal(Ia, Ib)
+
+
+def test_bits_only_and_replay_only(cuda):
+    H = W = 128
+    T = blob_target(H, W, 1006)
+    t = torch.from_numpy(T).to(cuda)
+    codes = pipeline.lut(2, 521, device=cuda)
+    b_full, I_full = pipeline.ospr(t, 5, codes, 521)
+    b_only, none_I = pipeline.ospr(t, 5, codes, 521, replay=False)
+    none_b, I_only = pipeline.ospr(t, 5, codes, 521, bits=False)
+    torch.cuda.synchronize()
+    assert none_I is None and none_b is None
+    assert torch.equal(b_full, b_only)
+    assert torch.equal(I_full, I_only)
+
+
+def test_deterministic(cuda):
+    H = W = 256
+    T = blob_target(H, W, 1007)
+    a = _gpu_ospr(cuda, T, 9, 10007, 4)
+    b = _gpu_ospr(cuda, T, 9, 10007, 4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_many_pairs_span_chunks(cuda):
+    # more pairs than one chunk holds: the column accumulator carries across chunks
+    H = W = 64
+    N = 37
+    T = blob_target(H, W, 1008)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, 10007, 6)
+    table = olut.lut_codes(6, 10007)
+    ob, oI, ex = oospr.ospr(T, N, table, 10007, 6, keep_fields=True)
+    check_bits(gb, ob, ex["re_h"], H * W)
+    check_replay(gI, oospr.replay_from_bits(gb, H, W))
+
+
+def test_full_size_1024_sampled(cuda):
+    """The benchmark workload (1024x1024, N = 24) in its launch configuration: sub-frames
+    0 and 23 element by element, the replay at sampled pixels by direct DFT sums of the
+    GPU's bits, the NMSE from the GPU replay."""
+    H = W = 1024
+    N, L, seed = 24, 10007, 7
+    T = blob_target(H, W, 1000)
+    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, N, L, seed)
+    table = olut.lut_codes(seed, L)
+    assert np.array_equal(gcodes, table)
+    P = H * W
+    for s in (0, N - 1):
+        c = olut.subframe_codes(table, L, seed, 0, s, P, P)
+        Hs = oospr.back_propagate(oospr.subframe_field(T, c))
+        ob = oospr.pack_bits(oospr.binarise(Hs.real))
+        check_bits(gb[s:s + 1], ob[None, :], [Hs.real], P)
+    hs = np.where(unpack(gb, P), -1.0, 1.0).reshape(N, H, W)
+    rng = np.random.default_rng(0)
+    pix = [(0, 0), (H // 2, W // 2)] + [tuple(rng.integers(0, H, 2)) for _ in range(10)]
+    r = np.arange(H)[:, None]
+    c = np.arange(W)[None, :]
+    for (u, v) in pix:
+        ph = np.exp(-2j * np.pi * (u * r / H + v * c / W))
+        R = np.tensordot(hs, ph, axes=([1, 2], [0, 1])) / np.sqrt(P)
+        Iuv = np.mean(np.abs(R) ** 2)
+        assert abs(gI[u, v] - Iuv) <= 1e-4 * gI.max(), (u, v, gI[u, v], Iuv)
+    o_stage = oerr.replay_error(gI, T)
+    check_nmse(gerr[2], o_stage[2])
