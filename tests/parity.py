@@ -33,7 +33,8 @@ def unpack(words, P):
 
 
 def check_bits(gpu_words, oracle_words, re_fields, P):
-    """Binarisation parity for N sub-frames; returns the agreement fraction."""
+    """Binarisation parity for N sub-frames; returns (agreement over decidable pixels,
+    fraction of undecidable pixels)."""
     g = unpack(gpu_words, P)
     o = unpack(oracle_words, P)
     diff = g != o
@@ -47,7 +48,7 @@ def check_bits(gpu_words, oracle_words, re_fields, P):
                 f"sub-frame {s}: a pixel with |Re H| = {worst:.3e} (> {RE_TIE * re.max():.3e}) flipped"
     agree = 1.0 - diff[decidable].mean()
     assert agree >= BIT_AGREE, f"binarised agreement {agree:.6f} over decidable pixels"
-    return agree
+    return agree, 1.0 - decidable.mean()
 
 
 def check_replay(gpu_I, oracle_I):

@@ -53,7 +53,7 @@ def test_parity_elementwise(cuda, H, W, N, L, kind):
     if L > 0:
         assert np.array_equal(gcodes, table)
     ob, oI, ex = oospr.ospr(T, N, table, L, seed, keep_fields=True)
-    check_bits(gb, ob, ex["re_h"], H * W)
+    _, undecidable = check_bits(gb, ob, ex["re_h"], H * W)
     # stage-wise replay: the oracle replays the GPU's bits
     I_from_bits = oospr.replay_from_bits(gb, H, W)
     check_replay(gI, I_from_bits)
@@ -61,9 +61,11 @@ def test_parity_elementwise(cuda, H, W, N, L, kind):
     o_stage = oerr.replay_error(gI, T)
     check_nmse(gerr[2], o_stage[2])
     check_nmse(gerr[1], o_stage[1])
-    # end to end against the oracle's own replay
-    o_e2e = oerr.replay_error(oI, T)
-    check_nmse(gerr[2], o_e2e[2])
+    # end to end against the oracle's own replay, where the binarisation is decidable
+    # (one table entry on a band-limited target leaves most of Re H at zero)
+    if undecidable < 1e-3:
+        o_e2e = oerr.replay_error(oI, T)
+        check_nmse(gerr[2], o_e2e[2])
 
 
 @pytest.mark.parametrize("levels", [2, 16])
