@@ -145,6 +145,38 @@ int ospr_generate(const float* d_target, int H, int W, int N,
                   uint32_t* d_holo_bits, float* d_replay,
                   void* d_ws, size_t ws_bytes, holo_stream_t s);
 
+/*
+ * ospr_generate_noalloc - ospr_generate for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment variant, not part of the method.
+ *
+ * Some callers can't call cudaMalloc or hand the library a workspace: a display
+ * pipeline with a hard per-frame deadline (cudaMalloc and cudaFree may synchronise the
+ * device and stall the frame), a plug-in inside a host application that owns every
+ * device allocation and exposes none, or firmware-style hosts whose device memory is
+ * partitioned once at start-up. This entry point takes the same arguments as
+ * ospr_generate minus the workspace and gives the same results (the bits are identical;
+ * the replay differs only in the float32 summation order of sub-frame pairs).
+ *
+ * Scratch: one file-scope device array of HOLO_NOALLOC_SCRATCH_BYTES (32 MiB), which
+ * every GPU that loads the library holds until the process exits. It fits one complex64
+ * and one float32 H*W field, so H*W <= 2^21 (e.g. 1024x1024 or 1024x2048); larger
+ * shapes return HOLO_EWORKSPACE with a message, and nothing is launched.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress, with that device current; make that first call before any
+ * stream capture.
+ * Every call on a device shares the one array and leaves its contents behind; a call
+ * writes every scratch byte before reading it, so no clearing is needed, but calls
+ * whose kernels overlap on the GPU (different streams, or host threads) race on the
+ * array and corrupt each other's results: serialise them.
+ * Errors: as ospr_generate, with HOLO_EWORKSPACE for shapes beyond the scratch.
+ */
+#define HOLO_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
+                          const uint8_t* d_codes, int64_t L, int levels, uint64_t seed,
+                          int64_t start_index, int64_t subframe_stride, int precision,
+                          uint32_t* d_holo_bits, float* d_replay, holo_stream_t s);
+
 /* --------------------------------------------------------------------- GS ---- */
 
 /*

@@ -21,6 +21,7 @@
 //   col_fft   columns: column DFT, S += |Z|^2 over the pairs of a group
 // then finalize: I(k) = (sum_g S_g(k) + S_g(-k)) / (2*N*H*W).
 #include <cmath>
+#include <mutex>
 
 #include "fft_core.cuh"
 #include "phase_source.cuh"
@@ -386,6 +387,119 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
         if (!is_prime(L)) warn("design rule: L=%lld is not prime", (long long)L);
         if (L <= N) warn("design rule: L=%lld is not greater than N=%d", (long long)L, N);
         if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
+    }
+    return HOLO_OK;
+}
+
+// ================================================= fixed-scratch variant ====
+// ospr_generate_noalloc: the same computation as ospr_generate for callers that cannot
+// allocate device memory. Its scratch is one file-scope device array of a fixed size,
+// shared by every call in the process; host code reaches it only through the address
+// cudaGetSymbolAddress returns for the current device.
+namespace holo {
+
+static __device__ __align__(256) unsigned char g_ospr_noalloc_scratch[HOLO_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];
+
+// Device address of the scratch array on the current device, looked up once per device.
+static int noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "ospr_generate_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(HOLO_EUNSUPPORTED, "ospr_generate_noalloc: device %d", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_ospr_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "ospr_generate_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return HOLO_OK;
+}
+
+// One partial accumulator and as many sub-frame pairs per chunk as the scratch holds.
+static bool noalloc_plan(int H, int W, int N, OsprPlan* pl) {
+    const size_t P = size_t(H) * W;
+    pl->npairs = (N + 1) / 2;
+    pl->groups = 1;
+    pl->s_bytes = align_up(P * sizeof(float), 256);
+    if (pl->s_bytes >= size_t(HOLO_NOALLOC_SCRATCH_BYTES)) return false;
+    const size_t fit = (size_t(HOLO_NOALLOC_SCRATCH_BYTES) - pl->s_bytes) / align_up(P * sizeof(float2), 256);
+    if (fit < 1) return false;
+    int chunk = pl->npairs < kMaxChunkPairs ? pl->npairs : kMaxChunkPairs;
+    if (size_t(chunk) > fit) chunk = int(fit);
+    pl->chunk = chunk;
+    pl->z_bytes = align_up(size_t(chunk) * P * sizeof(float2), 256);
+    pl->total = pl->z_bytes + pl->s_bytes;
+    return pl->total <= size_t(HOLO_NOALLOC_SCRATCH_BYTES);
+}
+
+}  // namespace holo
+
+extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
+                                     const uint8_t* d_codes, int64_t L, int levels, uint64_t seed,
+                                     int64_t start_index, int64_t subframe_stride, int precision,
+                                     uint32_t* d_holo_bits, float* d_replay, holo_stream_t s) {
+    clear_error();
+    const char* who = "ospr_generate_noalloc";
+    int rc = check_shape(who, H, W);
+    if (rc) return rc;
+    if (N < 1 || N > 4096) return fail(HOLO_EINVAL, "%s: N=%d out of [1, 4096]", who, N);
+    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "%s: precision %d is not built", who, precision);
+    if (!d_target) return fail(HOLO_EINVAL, "%s: d_target is NULL", who);
+    if (!d_holo_bits && !d_replay) return fail(HOLO_EINVAL, "%s: both outputs are NULL", who);
+    OsprPlan pl;
+    if (!noalloc_plan(H, W, N, &pl))
+        return fail(HOLO_EWORKSPACE,
+                    "%s: H=%d W=%d needs more than the fixed %u-byte scratch (one complex64 "
+                    "and one float32 H*W field); use ospr_generate with a workspace", who, H, W,
+                    unsigned(HOLO_NOALLOC_SCRATCH_BYTES));
+    const int64_t P = int64_t(H) * W;
+    const int64_t stride = subframe_stride == 0 ? P : subframe_stride;
+    if (stride > (INT64_C(1) << 40) || start_index > (INT64_C(1) << 61))
+        return fail(HOLO_EINVAL, "%s: start or stride too large", who);
+    PhaseSource ps;
+    rc = make_phase_source(who, d_codes, L, levels, seed, start_index, stride, &ps);
+    if (rc) return rc;
+    void* scratch = nullptr;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    Tables tab;
+    if ((rc = device_tables(&tab))) return rc;
+
+    OsprArgs a;
+    a.target = d_target;
+    a.H = H;
+    a.W = W;
+    a.N = N;
+    a.ps = ps;
+    a.zbuf = static_cast<float2*>(scratch);
+    a.sacc = reinterpret_cast<float*>(static_cast<char*>(scratch) + pl.z_bytes);
+    a.groups = pl.groups;
+    a.bits = d_holo_bits;
+    a.tw = tab.twiddles;
+    a.cs256 = tab.cs256;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    const bool replay = d_replay != nullptr;
+    // every scratch byte a kernel reads was written earlier in this call (the first chunk
+    // overwrites the accumulator), so nothing needs clearing between calls
+    for (int first = 0; first < pl.npairs; first += pl.chunk) {
+        a.first_pair = first;
+        a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
+        a.accumulate = first > 0;
+        if ((rc = run_col_ifft(a, st))) return rc;
+        if ((rc = run_row(a, replay, st))) return rc;
+        if (replay && (rc = run_col_fft(a, st))) return rc;
+    }
+    if (replay) {
+        const float scale = float(1.0 / (2.0 * double(N) * double(P)));
+        const int threads = 256;
+        const int blocks = int((P + threads - 1) / threads);
+        Launch ln("ospr_finalize", st);
+        k_ospr_finalize<<<blocks, threads, 0, st>>>(a.sacc, pl.groups, H, W, scale, d_replay);
+        if ((rc = ln.done("ospr_finalize launch"))) return rc;
     }
     return HOLO_OK;
 }

@@ -22,6 +22,7 @@ HOLO_ETIMEOUT = -4
 HOLO_ENOMEM = -5
 HOLO_EWORKSPACE = -6
 HOLO_FP32, HOLO_FP16X2, HOLO_BF16X2 = 0, 1, 2
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 L_UNREPEATED = -1
 
 _STATUS_NAMES = {0: "HOLO_OK", -1: "HOLO_EINVAL", -2: "HOLO_EUNSUPPORTED", -3: "HOLO_ECUDA",
@@ -51,6 +52,10 @@ _SIGS = {
                                  _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
                                  _c.c_int64, _c.c_int64, _c.c_int,
                                  _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "ospr_generate_noalloc": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int,
+                                         _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
+                                         _c.c_int64, _c.c_int64, _c.c_int,
+                                         _c.c_void_p, _c.c_void_p, _c.c_void_p]),
     "gs_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "gs_iterate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
                               _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
@@ -172,6 +177,14 @@ def ospr_generate(d_target, H, W, N, d_codes, L, levels, seed, start_index, subf
     return _call("ospr_generate", _ptr(d_target), H, W, N, _ptr(d_codes), L, levels, seed,
                  start_index, subframe_stride, precision, _ptr(d_holo_bits), _ptr(d_replay),
                  _ptr(d_ws), ws_bytes, _stream(stream, d_target))
+
+
+def ospr_generate_noalloc(d_target, H, W, N, d_codes, L, levels, seed, start_index,
+                          subframe_stride, precision, d_holo_bits, d_replay, stream=None):
+    """ospr_generate on the library's fixed scratch array (no workspace argument)."""
+    return _call("ospr_generate_noalloc", _ptr(d_target), H, W, N, _ptr(d_codes), L, levels, seed,
+                 start_index, subframe_stride, precision, _ptr(d_holo_bits), _ptr(d_replay),
+                 _stream(stream, d_target))
 
 
 def gs_workspace_size(H, W, iters, precision=HOLO_FP32):
