@@ -131,6 +131,8 @@ def kernel_bytes(family, P, pairs, groups, N):
         return groups * 4 * P + 4 * P
     if family in ("err_pass1", "err_pass2"):
         return 8 * P
+    if family == "err_finish":
+        return 0
     if family == "lut_build":
         return 0
     return None
@@ -220,15 +222,16 @@ def run_ours(args):
 
     # per-kernel durations from the library's event timing over the timed steps
     fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "err_pass1",
-            "err_pass2"]
+            "err_pass2", "err_finish"]
     prof = {f: holo.holo_profile_read(f) for f in fams}
     npairs = (N_SF + 1) // 2
-    groups = min(npairs, 4)
+    chunk = min(npairs, int(os.environ.get("HOLO_OSPR_CHUNK", "16")))
+    groups = min(chunk, int(os.environ.get("HOLO_OSPR_GROUPS", "4")))
     dom = max(fams, key=lambda f: prof[f][1])
     n_dom, ms_dom = prof[dom]
     peaks = _peaks()
     peak_bw = peaks["hbm_gbs"] if peaks else 6800.0
-    bytes_dom = kernel_bytes(dom, P, npairs, groups, N_SF)
+    bytes_dom = kernel_bytes(dom, P, chunk, groups, N_SF)
     achieved = bytes_dom / (ms_dom / n_dom / 1e3) / 1e9 if n_dom and bytes_dom else None
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
                 "frac": achieved / peak_bw if achieved else None, "traffic": None,

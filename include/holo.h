@@ -76,7 +76,8 @@ int holo_launch_count(uint64_t* out_count);
  * for the kernel family `name`, the number of launches and their summed duration in
  * milliseconds since the last holo_profile_reset. Families: "lut_build",
  * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "gs_prepare",
- * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2". */
+ * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2",
+ * "err_finish". */
 int holo_profile_enable(int on);
 int holo_profile_reset(void);
 int holo_profile_read(const char* name, uint64_t* launches, double* total_ms);
@@ -134,7 +135,10 @@ int ospr_workspace_size(int H, int W, int N, int precision, size_t* bytes);
  *                of that sub-frame, 1 for -1.
  *   d_replay     [H][W] float32 output or NULL: mean replay intensity over sub-frames.
  *   d_ws         device workspace of at least ospr_workspace_size() bytes, 256-byte
- *                aligned.
+ *                aligned. Sub-frame pairs go through the transforms in chunks of up to
+ *                16 pairs (environment override HOLO_OSPR_CHUNK=1..16, read once per
+ *                process; HOLO_OSPR_GROUPS=1..4 sets the partial accumulators); the
+ *                workspace size follows the same setting.
  * Design-rule warnings (Section 8: L prime, L > N, L > max(H, W)) are returned with
  * HOLO_OK and a message in holo_last_error(). Errors: HOLO_EINVAL, HOLO_EUNSUPPORTED,
  * HOLO_EWORKSPACE, HOLO_ECUDA.

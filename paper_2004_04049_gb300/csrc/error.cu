@@ -2,121 +2,170 @@
 // optimal-scale reading: alpha = sum(I T^2)/sum(I^2), mse = sum((alpha I - T^2)^2)/P,
 // nmse = sum((alpha I - T^2)^2)/sum(T^4).
 //
-// Two passes (alpha must be known before the residual sum). Each thread forms its terms
-// with single-rounding fmaf in float32 over a handful of pixels; every sum across threads
-// and blocks is float64 with a fixed reduction order, so results are bit-reproducible.
-// The kernels are HBM-bound: 8 bytes per pixel per pass (+1 with a mask).
-#include "reduce.cuh"
+// Three launches, no atomics:
+//   partials1  per block: sum I*T^2, sum I^2, sum T^4, count
+//   partials2  every block first reduces partials1 to alpha (one warp, fixed order, so
+//              every block gets the same bits), then its share of sum (alpha I - T^2)^2
+//   finish     one warp: mse and nmse from partials2
+// Each thread forms its terms with single-rounding fmaf in float32 over a few pixels;
+// every sum across threads, warps and blocks is float-float (about 48 significant bits,
+// ffloat.cuh) in a fixed order, so results are bit-reproducible, and only the three
+// reported values are converted to float64. HBM-bound: 8 bytes per pixel per pass (+1
+// with a mask).
+#include "ffloat.cuh"
 #include "runtime.h"
 
 namespace holo {
 
 constexpr int kErrThreads = 256;
-constexpr int kErrMaxBlocks = 152 * 8;
-
-struct ErrWs {
-    unsigned int ticket[2];
-    unsigned int pad[62];
-    double alpha, s_tt, count, pad2[29];
-};
+constexpr int kErrMaxBlocks = 152 * 2;
 
 static int err_blocks(int64_t P) {
-    int64_t nb = (P / 4 + kErrThreads - 1) / kErrThreads;
+    int64_t nb = (P / 16 + kErrThreads - 1) / kErrThreads;
     if (nb < 1) nb = 1;
     return int(nb < kErrMaxBlocks ? nb : kErrMaxBlocks);
 }
 
 __device__ __forceinline__ float mask_at(const uint8_t* m, int64_t i) { return m ? (m[i] ? 1.f : 0.f) : 1.f; }
 
+// Every thread owns up to kErrVec float4 groups of pixels (q = tid + k*nth) and issues
+// all of their loads before any arithmetic, so a pass costs about one memory latency
+// instead of one per grid-stride iteration.
+constexpr int kErrVec = 4;
+
+struct ErrTile {
+    float4 i[kErrVec], t[kErrVec];
+};
+
+__device__ __forceinline__ void err_load(const float* __restrict__ I, const float* __restrict__ T,
+                                         int64_t q0, int64_t nth, int64_t P4, ErrTile& x) {
+#pragma unroll
+    for (int k = 0; k < kErrVec; ++k) {
+        const int64_t q = q0 + k * nth;
+        x.i[k] = q < P4 ? __ldg(reinterpret_cast<const float4*>(I) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        x.t[k] = q < P4 ? __ldg(reinterpret_cast<const float4*>(T) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ float4 mask4(const uint8_t* __restrict__ m, int64_t q, int64_t P4) {
+    if (!m || q >= P4) return make_float4(q < P4 ? 1.f : 0.f, q < P4 ? 1.f : 0.f, q < P4 ? 1.f : 0.f,
+                                          q < P4 ? 1.f : 0.f);
+    const uchar4 b = reinterpret_cast<const uchar4*>(m)[q];
+    return make_float4(b.x ? 1.f : 0.f, b.y ? 1.f : 0.f, b.z ? 1.f : 0.f, b.w ? 1.f : 0.f);
+}
+
+// partials laid out [k][nb]: k = 0 sum I T^2, 1 sum I^2, 2 sum T^4, 3 count
 __global__ void __launch_bounds__(kErrThreads)
 k_err_pass1(const float* __restrict__ I, const float* __restrict__ T, const uint8_t* __restrict__ mask,
-            int64_t P, ErrWs* ws, double* partials, double* d_out) {
-    __shared__ double sm[32];
-    __shared__ int s_last;
-    float sit = 0.f, sii = 0.f, stt = 0.f, cnt = 0.f;
+            int64_t P, ff* __restrict__ partials) {
+    __shared__ ff sm[32 * 4];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
-    const bool vec = ((reinterpret_cast<uintptr_t>(I) | reinterpret_cast<uintptr_t>(T)) & 15) == 0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(I) | reinterpret_cast<uintptr_t>(T) |
+                       reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
     const int64_t P4 = vec ? P / 4 : 0;
-    for (int64_t q = tid; q < P4; q += nth) {
-        const float4 i4 = __ldg(reinterpret_cast<const float4*>(I) + q);
-        const float4 t4 = __ldg(reinterpret_cast<const float4*>(T) + q);
-        const float iv[4] = {i4.x, i4.y, i4.z, i4.w}, tv[4] = {t4.x, t4.y, t4.z, t4.w};
+    for (int64_t q0 = tid; q0 < P4; q0 += kErrVec * nth) {
+        ErrTile x;
+        err_load(I, T, q0, nth, P4, x);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float m = mask_at(mask, 4 * q + k);
-            const float t2 = tv[k] * tv[k] * m, i1 = iv[k] * m;
-            sit = fmaf(i1, t2, sit);
-            sii = fmaf(i1, i1, sii);
-            stt = fmaf(t2, t2, stt);
-            cnt += m;
+        for (int k = 0; k < kErrVec; ++k) {
+            const float4 m4 = mask4(mask, q0 + k * nth, P4);
+            const float iv[4] = {x.i[k].x, x.i[k].y, x.i[k].z, x.i[k].w};
+            const float tv[4] = {x.t[k].x, x.t[k].y, x.t[k].z, x.t[k].w};
+            const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float t2 = tv[j] * tv[j] * mv[j], i1 = iv[j] * mv[j];
+                acc[0] = fmaf(i1, t2, acc[0]);
+                acc[1] = fmaf(i1, i1, acc[1]);
+                acc[2] = fmaf(t2, t2, acc[2]);
+                acc[3] += mv[j];
+            }
         }
     }
     for (int64_t i = 4 * P4 + tid; i < P; i += nth) {
         const float m = mask_at(mask, i);
         const float t2 = T[i] * T[i] * m, i1 = I[i] * m;
-        sit = fmaf(i1, t2, sit);
-        sii = fmaf(i1, i1, sii);
-        stt = fmaf(t2, t2, stt);
-        cnt += m;
+        acc[0] = fmaf(i1, t2, acc[0]);
+        acc[1] = fmaf(i1, i1, acc[1]);
+        acc[2] = fmaf(t2, t2, acc[2]);
+        acc[3] += m;
     }
-    const int nb = gridDim.x;
-    double v[4] = {sit, sii, stt, cnt};
-    for (int k = 0; k < 4; ++k) {
-        const double b = block_sum(v[k], sm);
-        if (threadIdx.x == 0) partials[k * nb + blockIdx.x] = b;
-    }
-    if (!grid_partial_done(0.0, partials + 4 * nb, &ws->ticket[0], &s_last)) return;
-    double tot[4];
-    for (int k = 0; k < 4; ++k) tot[k] = sum_partials(partials + k * nb, nb, sm);
+    ff b[4];
+    block_sums_ff<4>(acc, b, sm);
     if (threadIdx.x == 0) {
-        const double alpha = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
-        ws->alpha = alpha;
-        ws->s_tt = tot[2];
-        ws->count = tot[3];
-        d_out[0] = alpha;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partials[k * gridDim.x + blockIdx.x] = b[k];
     }
 }
 
 __global__ void __launch_bounds__(kErrThreads)
 k_err_pass2(const float* __restrict__ I, const float* __restrict__ T, const uint8_t* __restrict__ mask,
-            int64_t P, ErrWs* ws, double* partials, double* d_out) {
-    __shared__ double sm[32];
-    __shared__ int s_last;
-    const float alpha = float(ws->alpha);
-    float sse = 0.f;
+            int64_t P, const ff* __restrict__ partials1, ff* __restrict__ partials2,
+            double* __restrict__ d_out) {
+    __shared__ ff sm[32];
+    __shared__ float s_alpha;
+    const int nb = gridDim.x;
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
-    const bool vec = ((reinterpret_cast<uintptr_t>(I) | reinterpret_cast<uintptr_t>(T)) & 15) == 0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(I) | reinterpret_cast<uintptr_t>(T) |
+                       reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
     const int64_t P4 = vec ? P / 4 : 0;
-    for (int64_t q = tid; q < P4; q += nth) {
-        const float4 i4 = __ldg(reinterpret_cast<const float4*>(I) + q);
-        const float4 t4 = __ldg(reinterpret_cast<const float4*>(T) + q);
-        const float iv[4] = {i4.x, i4.y, i4.z, i4.w}, tv[4] = {t4.x, t4.y, t4.z, t4.w};
+    // first tile's loads go out before the wait for alpha
+    ErrTile x;
+    err_load(I, T, tid, nth, P4, x);
+    if (threadIdx.x < 32) {
+        const ff s_it = warp_sum_array_ff(partials1, nb);
+        const ff s_ii = warp_sum_array_ff(partials1 + nb, nb);
+        const ff alpha = s_ii.hi > 0.f ? ff_div(s_it, s_ii) : ff_make(0.f);
+        if (threadIdx.x == 0) {
+            s_alpha = alpha.hi;
+            if (blockIdx.x == 0) d_out[0] = ff_to_double(alpha);
+        }
+    }
+    __syncthreads();
+    const float alpha = s_alpha;
+    float acc[1] = {0.f};
+    for (int64_t q0 = tid; q0 < P4; q0 += kErrVec * nth) {
+        if (q0 != tid) err_load(I, T, q0, nth, P4, x);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float d = fmaf(alpha, iv[k], -tv[k] * tv[k]) * mask_at(mask, 4 * q + k);
-            sse = fmaf(d, d, sse);
+        for (int k = 0; k < kErrVec; ++k) {
+            const float4 m4 = mask4(mask, q0 + k * nth, P4);
+            const float iv[4] = {x.i[k].x, x.i[k].y, x.i[k].z, x.i[k].w};
+            const float tv[4] = {x.t[k].x, x.t[k].y, x.t[k].z, x.t[k].w};
+            const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float d = fmaf(alpha, iv[j], -tv[j] * tv[j]) * mv[j];
+                acc[0] = fmaf(d, d, acc[0]);
+            }
         }
     }
     for (int64_t i = 4 * P4 + tid; i < P; i += nth) {
         const float d = fmaf(alpha, I[i], -T[i] * T[i]) * mask_at(mask, i);
-        sse = fmaf(d, d, sse);
+        acc[0] = fmaf(d, d, acc[0]);
     }
-    const int nb = gridDim.x;
-    const double b = block_sum(double(sse), sm);
-    if (!grid_partial_done(b, partials, &ws->ticket[1], &s_last)) return;
-    const double tot = sum_partials(partials, nb, sm);
+    ff b[1];
+    block_sums_ff<1>(acc, b, sm);
+    if (threadIdx.x == 0) partials2[blockIdx.x] = b[0];
+}
+
+__global__ void __launch_bounds__(32)
+k_err_finish(const ff* __restrict__ partials1, const ff* __restrict__ partials2, int nb,
+             double* __restrict__ d_out) {
+    const ff s_tt = warp_sum_array_ff(partials1 + 2 * nb, nb);
+    const ff count = warp_sum_array_ff(partials1 + 3 * nb, nb);
+    const ff sse = warp_sum_array_ff(partials2, nb);
     if (threadIdx.x == 0) {
-        d_out[1] = ws->count > 0.0 ? tot / ws->count : 0.0;
-        d_out[2] = ws->s_tt > 0.0 ? tot / ws->s_tt : 0.0;
+        d_out[1] = count.hi > 0.f ? ff_to_double(ff_div(sse, count)) : 0.0;
+        d_out[2] = s_tt.hi > 0.f ? ff_to_double(ff_div(sse, s_tt)) : 0.0;
     }
 }
 
 static size_t err_ws_bytes(int64_t P) {
     const int nb = err_blocks(P);
-    return align_up(sizeof(ErrWs), 256) + align_up(sizeof(double) * size_t(nb) * 5, 256) +
-           align_up(sizeof(double) * size_t(nb), 256);
+    return align_up(sizeof(ff) * size_t(nb) * 4, 256) + align_up(sizeof(ff) * size_t(nb), 256);
 }
 
 }  // namespace holo
@@ -145,18 +194,21 @@ extern "C" int replay_error(const float* d_replay, const float* d_target, const 
     if (!d_ws || ws_bytes < need) return fail(HOLO_EWORKSPACE, "%s: workspace %zu bytes, need %zu", who, ws_bytes, need);
     if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) return fail(HOLO_EWORKSPACE, "%s: workspace not 256-byte aligned", who);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-    ErrWs* ws = static_cast<ErrWs*>(d_ws);
-    double* part1 = reinterpret_cast<double*>(static_cast<char*>(d_ws) + align_up(sizeof(ErrWs), 256));
     const int nb = err_blocks(P);
-    double* part2 = part1 + align_up(sizeof(double) * size_t(nb) * 5, 256) / sizeof(double);
-    int rc = cuda_status(cudaMemsetAsync(ws->ticket, 0, sizeof(ws->ticket), st), "replay_error: reset");
-    if (rc) return rc;
+    ff* part1 = static_cast<ff*>(d_ws);
+    ff* part2 = part1 + align_up(sizeof(ff) * size_t(nb) * 4, 256) / sizeof(ff);
+    int rc;
     {
         Launch ln("err_pass1", st);
-        k_err_pass1<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, ws, part1, d_out);
+        k_err_pass1<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1);
         if ((rc = ln.done("err_pass1 launch"))) return rc;
     }
-    Launch ln("err_pass2", st);
-    k_err_pass2<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, ws, part2, d_out);
-    return ln.done("err_pass2 launch");
+    {
+        Launch ln("err_pass2", st);
+        k_err_pass2<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1, part2, d_out);
+        if ((rc = ln.done("err_pass2 launch"))) return rc;
+    }
+    Launch ln("err_finish", st);
+    k_err_finish<<<1, 32, 0, st>>>(part1, part2, nb, d_out);
+    return ln.done("err_finish launch");
 }

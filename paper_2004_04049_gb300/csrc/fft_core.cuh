@@ -83,8 +83,15 @@ __host__ __device__ constexpr int stage_offset(int N, int R, int s) {
 constexpr int kTwiddleTotal = twiddle_total();
 
 // line buffer: one float2 of padding every R entries (bank spread of the stage stores),
-// plus one so that consecutive line buffers start on different banks
+// plus an offset so that the line buffers of the lanes sharing a half-warp start on
+// different banks: rows use one line per warp (offset 1); a column pass puts LPC
+// consecutive columns on consecutive lanes and 16/LPC thread indices t of each column in
+// a half-warp, so its line stride is 16/LPC (mod 16) and lane (lc, t) lands on bank
+// lc*16/LPC + t.
 __host__ __device__ constexpr int line_stride(int N, int R) { return N + N / R + 1; }
+__host__ __device__ constexpr int col_line_stride(int N, int R, int LPC) {
+    return N + N / R + (LPC >= 16 ? 1 : 16 / LPC);
+}
 template <int R>
 __device__ __forceinline__ int pad_index(int i) { return i + i / R; }
 
@@ -204,6 +211,27 @@ __device__ __forceinline__ void line_fft(float2 (&v)[R], float2* buf, int t,
     static_assert(N % R == 0 && R <= 32, "bad FFT plan");
     if constexpr (stage_count(N, R) > 1) line_sync<BLOCK>();   // buffer may still be read by a previous use
     LineStage<N, R, DIR, BLOCK, 0>::run(v, buf, t, tw);
+}
+
+// ------------------------------------------- replicated cos/sin table ----
+// The 256-entry (cos, sin) table replicated COPIES times in shared memory: entry c of
+// copy k sits at [c*COPIES + k] and lane l reads copy l mod COPIES. With 16 copies the
+// 16 lanes of a half-warp hit 16 different banks whatever codes they look up (random
+// codes would otherwise collide); a kernel that looks up few codes per table load uses
+// one copy.
+template <int COPIES>
+constexpr int cs_smem_entries() { return 256 * COPIES; }
+constexpr int kCsCopies = 16;
+constexpr int kCsSmemEntries = 256 * kCsCopies;
+
+template <int COPIES = kCsCopies>
+__device__ __forceinline__ void load_cs_table(float2* sm, const float2* __restrict__ cs256) {
+    for (int i = threadIdx.x; i < 256 * COPIES; i += blockDim.x) sm[i] = __ldg(cs256 + i / COPIES);
+}
+// (cos, sin)(2*pi*i/256) for i < 256
+template <int COPIES = kCsCopies>
+__device__ __forceinline__ float2 cs_lookup(const float2* sm, uint32_t i) {
+    return sm[i * COPIES + (threadIdx.x & (COPIES - 1))];
 }
 
 // --------------------------------------------------------------- helpers ----

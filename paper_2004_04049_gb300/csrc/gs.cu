@@ -15,9 +15,9 @@
 //   finish     per-iteration float64 error sums
 #include <cmath>
 
+#include "ffloat.cuh"
 #include "fft_core.cuh"
 #include "phase_source.cuh"
-#include "reduce.cuh"
 #include "runtime.h"
 
 namespace holo {
@@ -44,11 +44,8 @@ constexpr int kGsPrepThreads = 256;
 constexpr int kGsPrepBlocks = 152;
 
 struct GsScalars {
-    unsigned int ticket;
-    unsigned int pad[63];
-    double sum_t2;
-    float scale;        // sqrt(P / sum T^2)
-    float pad2[61];
+    float scale;        // sqrt(P / sum T^2), written by k_gs_col_init
+    float pad[63];
 };
 
 struct GsArgs {
@@ -59,7 +56,8 @@ struct GsArgs {
     const float2* state_in;      // or a saved field
     float2* y;                   // [H][W] complex work field
     GsScalars* sc;
-    double* err_part;            // [iters][col blocks]
+    const ff* prep_part;         // [kGsPrepBlocks] partial sums of T^2
+    ff* err_part;                // [iters][col blocks] partial error sums
     int iter;
     uint8_t* codes_out;
     float* replay_out;
@@ -70,8 +68,11 @@ struct GsArgs {
 };
 
 template <int NC>
+constexpr int gs_col_stride() { return col_line_stride(NC, GsColCfg<NC>::R, GsColCfg<NC>::LPC); }
+// col_init and row also hold one copy of the cos/sin table (one lookup per pixel)
+template <int NC>
 constexpr size_t gs_col_smem() {
-    return sizeof(float2) * (256 + size_t(GsColCfg<NC>::LPC) * line_stride(NC, GsColCfg<NC>::R));
+    return sizeof(float2) * (256 + size_t(GsColCfg<NC>::LPC) * gs_col_stride<NC>());
 }
 template <int NR>
 constexpr size_t gs_row_smem() {
@@ -79,20 +80,22 @@ constexpr size_t gs_row_smem() {
 }
 
 // ----------------------------------------------------------------- prepare ----
+// per-block float-float partials of sum T^2
 __global__ void __launch_bounds__(kGsPrepThreads)
-k_gs_prepare(const float* __restrict__ T, int64_t P, GsScalars* sc, double* partials) {
-    __shared__ double sm[32];
-    __shared__ int s_last;
-    float acc = 0.f;
+k_gs_prepare(const float* __restrict__ T, int64_t P, ff* __restrict__ partials) {
+    __shared__ ff sm[32];
+    float acc[1] = {0.f};
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P; i += int64_t(gridDim.x) * blockDim.x)
-        acc = fmaf(T[i], T[i], acc);
-    const double b = block_sum(double(acc), sm);
-    if (!grid_partial_done(b, partials, &sc->ticket, &s_last)) return;
-    const double tot = sum_partials(partials, gridDim.x, sm);
-    if (threadIdx.x == 0) {
-        sc->sum_t2 = tot;
-        sc->scale = tot > 0.0 ? float(sqrt(double(P) / tot)) : 0.f;
-    }
+        acc[0] = fmaf(T[i], T[i], acc[0]);
+    ff b[1];
+    block_sums_ff<1>(acc, b, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = b[0];
+}
+
+// scale = sqrt(P / sum T^2), reduced by one warp in a fixed order (same bits in every block)
+__device__ __forceinline__ float gs_scale(const ff* __restrict__ partials, int64_t P) {
+    const ff tot = warp_sum_array_ff(partials, kGsPrepBlocks);
+    return tot.hi > 0.f ? sqrtf(ff_div(ff_make(float(P)), tot).hi) : 0.f;
 }
 
 // --------------------------------------------------------------- col_init ----
@@ -103,12 +106,21 @@ k_gs_col_init(GsArgs a) {
     extern __shared__ float2 sm[];
     float2* cs = sm;
     float2* lines = sm + 256;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) cs[i] = a.cs256[i];
+    load_cs_table<1>(cs, a.cs256);
+    __syncthreads();
+    __shared__ float s_scale;
+    if (threadIdx.x < 32) {
+        const float sc = gs_scale(a.prep_part, int64_t(a.H) * a.W);
+        if (threadIdx.x == 0) {
+            s_scale = sc;
+            if (blockIdx.x == 0) a.sc->scale = sc;
+        }
+    }
     __syncthreads();
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
-    const float scale = a.sc->scale;
+    const float scale = s_scale;
     const SubframeDraw d0 = subframe_draw(a.ps, 0);
     float2 v[R];
 #pragma unroll
@@ -120,11 +132,11 @@ k_gs_col_init(GsArgs a) {
             const float ts = __ldg(a.target + p) * scale;
             float2 ph;
             if (a.init_phase) sincosf(__ldg(a.init_phase + p), &ph.y, &ph.x);
-            else ph = cs[draw_code(a.ps, d0, p) << a.ps.cs_shift];
+            else ph = cs_lookup<1>(cs, draw_code(a.ps, d0, p) << a.ps.cs_shift);
             v[e] = make_float2(ts * ph.x, ts * ph.y);
         }
     }
-    line_fft<NC, R, +1, true>(v, lines + lc * line_stride(NC, R), t, a.tw);
+    line_fft<NC, R, +1, true>(v, lines + lc * gs_col_stride<NC>(), t, a.tw);
 #pragma unroll
     for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
 }
@@ -138,7 +150,7 @@ k_gs_row(GsArgs a) {
     extern __shared__ float2 sm[];
     float2* cs = sm;
     float2* lines = sm + 256;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) cs[i] = a.cs256[i];
+    load_cs_table<1>(cs, a.cs256);
     __syncthreads();
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int r = blockIdx.x * GsRowCfg<NR>::LPR + line;
@@ -156,7 +168,7 @@ k_gs_row(GsArgs a) {
         const float ang = atan2f(v[e].y, v[e].x);
         const int q = int(floorf(fmaf(ang, k_code, 0.5f))) & (levels - 1);
         if (a.codes_out) a.codes_out[size_t(r) * NR + t + T * e] = uint8_t(q);
-        v[e] = cs[q << shift];
+        v[e] = cs_lookup<1>(cs, uint32_t(q) << shift);
     }
     line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
 #pragma unroll
@@ -169,12 +181,12 @@ __global__ void __launch_bounds__((NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC)
 k_gs_col(GsArgs a) {
     constexpr int R = GsColCfg<NC>::R, LPC = GsColCfg<NC>::LPC, T = NC / R;
     extern __shared__ float2 sm[];
-    __shared__ double red[32];
-    float2* lines = sm + 256;
+    __shared__ ff red[32];
+    float2* lines = sm;
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
-    float2* buf = lines + lc * line_stride(NC, R);
+    float2* buf = lines + lc * gs_col_stride<NC>();
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = a.y[size_t(t + T * e) * W + c];
@@ -200,8 +212,10 @@ k_gs_col(GsArgs a) {
         }
         v[e] = En;
     }
-    const double b = block_sum(double(err), red);
-    if (threadIdx.x == 0) a.err_part[size_t(a.iter) * gridDim.x + blockIdx.x] = b;
+    const float errv[1] = {err};
+    ff b[1];
+    block_sums_ff<1>(errv, b, red);
+    if (threadIdx.x == 0) a.err_part[size_t(a.iter) * gridDim.x + blockIdx.x] = b[0];
     if constexpr (!LAST) {
         line_fft<NC, R, +1, true>(v, buf, t, a.tw);
 #pragma unroll
@@ -210,10 +224,10 @@ k_gs_col(GsArgs a) {
 }
 
 // ----------------------------------------------------------------- finish ----
-__global__ void k_gs_finish(const double* __restrict__ err_part, int nb, double* __restrict__ err) {
-    __shared__ double sm[32];
-    const double v = sum_partials(err_part + size_t(blockIdx.x) * nb, nb, sm);
-    if (threadIdx.x == 0) err[blockIdx.x] = v;
+__global__ void __launch_bounds__(32)
+k_gs_finish(const ff* __restrict__ err_part, int nb, double* __restrict__ err) {
+    const ff v = warp_sum_array_ff(err_part + size_t(blockIdx.x) * nb, nb);
+    if (threadIdx.x == 0) err[blockIdx.x] = ff_to_double(v);
 }
 
 // ------------------------------------------------------------------- host ----
@@ -240,7 +254,7 @@ static int launch_row(const GsArgs& a, cudaStream_t st) {
 template <int NC>
 static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
     static uint64_t mask0 = 0, mask1 = 0;
-    constexpr size_t smem = gs_col_smem<NC>();
+    constexpr size_t smem = sizeof(float2) * size_t(GsColCfg<NC>::LPC) * gs_col_stride<NC>();
     const int grid = a.W / GsColCfg<NC>::LPC, threads = (NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC;
     int rc = last ? ensure_smem((const void*)k_gs_col<NC, true>, smem, &mask1)
                   : ensure_smem((const void*)k_gs_col<NC, false>, smem, &mask0);
@@ -299,8 +313,8 @@ static GsLayout gs_layout(int H, int W, int iters) {
     l.y_off = 0;
     l.sc_off = align_up(P * sizeof(float2), 256);
     l.prep_off = l.sc_off + align_up(sizeof(GsScalars), 256);
-    l.err_off = l.prep_off + align_up(sizeof(double) * kGsPrepBlocks, 256);
-    l.total = l.err_off + align_up(sizeof(double) * size_t(iters) * size_t(col_blocks(H, W)), 256);
+    l.err_off = l.prep_off + align_up(sizeof(ff) * kGsPrepBlocks, 256);
+    l.total = l.err_off + align_up(sizeof(ff) * size_t(iters) * size_t(col_blocks(H, W)), 256);
     return l;
 }
 
@@ -366,7 +380,7 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
     a.state_in = reinterpret_cast<const float2*>(d_state_in);
     a.y = reinterpret_cast<float2*>(ws + lay.y_off);
     a.sc = reinterpret_cast<GsScalars*>(ws + lay.sc_off);
-    a.err_part = reinterpret_cast<double*>(ws + lay.err_off);
+    a.err_part = reinterpret_cast<ff*>(ws + lay.err_off);
     a.iter = 0;
     a.codes_out = nullptr;
     a.replay_out = d_replay;
@@ -376,12 +390,11 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
     a.inv_sqrt_p = float(1.0 / std::sqrt(double(H) * double(W)));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
 
-    rc = cuda_status(cudaMemsetAsync(&a.sc->ticket, 0, sizeof(unsigned int), st), "gs_iterate: reset");
-    if (rc) return rc;
+    a.prep_part = reinterpret_cast<const ff*>(ws + lay.prep_off);
     {
         Launch ln("gs_prepare", st);
-        k_gs_prepare<<<kGsPrepBlocks, kGsPrepThreads, 0, st>>>(d_target, int64_t(H) * W, a.sc,
-                                                               reinterpret_cast<double*>(ws + lay.prep_off));
+        k_gs_prepare<<<kGsPrepBlocks, kGsPrepThreads, 0, st>>>(d_target, int64_t(H) * W,
+                                                               reinterpret_cast<ff*>(ws + lay.prep_off));
         if ((rc = ln.done("gs_prepare launch"))) return rc;
     }
     if ((rc = run_col_init(a, st))) return rc;
@@ -394,7 +407,7 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
     }
     if (d_err) {
         Launch ln("gs_finish", st);
-        k_gs_finish<<<iters, 256, 0, st>>>(a.err_part, col_blocks(H, W), d_err);
+        k_gs_finish<<<iters, 32, 0, st>>>(a.err_part, col_blocks(H, W), d_err);
         if ((rc = ln.done("gs_finish launch"))) return rc;
     }
     if (use_lut && L > 0) {

@@ -21,6 +21,7 @@
 //   col_fft   columns: column DFT, S += |Z|^2 over the pairs of a group
 // then finalize: I(k) = (sum_g S_g(k) + S_g(-k)) / (2*N*H*W).
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "fft_core.cuh"
@@ -67,8 +68,15 @@ struct OsprArgs {
 };
 
 template <int NC>
-constexpr size_t col_smem_bytes() {
-    return sizeof(float2) * (256 + size_t(ColCfg<NC>::LPC) * line_stride(NC, ColCfg<NC>::R));
+constexpr int col_stride() { return col_line_stride(NC, ColCfg<NC>::R, ColCfg<NC>::LPC); }
+// pass 1 also holds the replicated cos/sin table
+template <int NC>
+constexpr size_t col_ifft_smem_bytes() {
+    return sizeof(float2) * (kCsSmemEntries + size_t(ColCfg<NC>::LPC) * col_stride<NC>());
+}
+template <int NC>
+constexpr size_t col_fft_smem_bytes() {
+    return sizeof(float2) * size_t(ColCfg<NC>::LPC) * col_stride<NC>();
 }
 template <int NR>
 constexpr size_t row_smem_bytes() {
@@ -76,49 +84,123 @@ constexpr size_t row_smem_bytes() {
 }
 
 // ------------------------------------------------------------------ pass 1 ----
+// Z for one column of one pair, in canonical layout (slot e <-> row t + T*e). MODE and
+// SINGLE are compile-time so that the element loops hold no branches: for each batch of
+// kBatch elements every load (target, mirror target, four codes) is issued before any
+// of them is used.
+constexpr int kBatch = 8;
+
+template <int NC, int MODE, bool SINGLE>
+__device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC>::R], const OsprArgs& a,
+                                                  const float2* cs, int t, int c, int s0) {
+    constexpr int R = ColCfg<NC>::R, T = NC / R;
+    constexpr int B = R < kBatch ? R : kBatch;
+    const int W = a.W;
+    const int cm = (W - c) & (W - 1);
+    const int sh = a.ps.cs_shift;
+    const SubframeDraw d0 = subframe_draw(a.ps, s0);
+    const SubframeDraw d1 = subframe_draw(a.ps, SINGLE ? s0 : s0 + 1);
+    // table mode: indices (start + s*stride + p) mod L advance by D = T*W mod L per element;
+    // the mirror pixel of row r = t + T*e is (H - r)*W + cm = q0 - e*T*W, except for row 0
+    const uint32_t L = a.ps.L;
+    const uint64_t fm = a.ps.fm;
+    uint32_t D = 0, i0 = 0, i1 = 0, m0 = 0, m1 = 0, z0 = 0, z1 = 0;
+    if constexpr (MODE == kPhaseTable) {
+        D = uint32_t((uint64_t(T) * uint64_t(W)) % L);
+        const uint32_t p0 = uint32_t(t) * uint32_t(W) + uint32_t(c);
+        const uint32_t q0 = uint32_t(NC - t) * uint32_t(W) + uint32_t(cm);
+        i0 = fastmod_u32(d0.base_mod + p0, fm, L);
+        i1 = fastmod_u32(d1.base_mod + p0, fm, L);
+        m0 = fastmod_u32(d0.base_mod + q0, fm, L);
+        m1 = fastmod_u32(d1.base_mod + q0, fm, L);
+        z0 = fastmod_u32(d0.base_mod + uint32_t(cm), fm, L);
+        z1 = fastmod_u32(d1.base_mod + uint32_t(cm), fm, L);
+    }
+    const int gshift = 64 - a.ps.bits;
+#pragma unroll
+    for (int e0 = 0; e0 < R; e0 += B) {
+        float tp[B], tm[B];
+        uint32_t pk[B];   // codes of (s0, p), (s0, -p), (s1, p), (s1, -p), one byte each
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int e = e0 + k;
+            const int r = t + T * e;
+            const int rm = (NC - r) & (NC - 1);
+            tp[k] = __ldg(a.target + r * W + c);
+            tm[k] = SINGLE ? 0.f : __ldg(a.target + rm * W + cm);
+            if constexpr (MODE == kPhaseTable) {
+                const uint32_t jm0 = (e == 0 && t == 0) ? z0 : m0;
+                const uint32_t jm1 = (e == 0 && t == 0) ? z1 : m1;
+                uint32_t w = __ldg(a.ps.codes + i0);
+                if constexpr (!SINGLE) {
+                    w |= uint32_t(__ldg(a.ps.codes + jm0)) << 8;
+                    w |= uint32_t(__ldg(a.ps.codes + i1)) << 16;
+                    w |= uint32_t(__ldg(a.ps.codes + jm1)) << 24;
+                }
+                pk[k] = w;
+                i0 += D; i0 -= (i0 >= L) ? L : 0u;
+                i1 += D; i1 -= (i1 >= L) ? L : 0u;
+                m0 = (m0 >= D) ? m0 - D : m0 + (L - D);
+                m1 = (m1 >= D) ? m1 - D : m1 + (L - D);
+            } else if constexpr (MODE == kPhaseGenerator) {
+                const uint64_t p = uint64_t(r) * uint64_t(W) + uint64_t(c);
+                const uint64_t pm = uint64_t(rm) * uint64_t(W) + uint64_t(cm);
+                uint32_t w = uint32_t(splitmix64_at(a.ps.seed, d0.base + p) >> gshift);
+                if constexpr (!SINGLE) {
+                    w |= uint32_t(splitmix64_at(a.ps.seed, d0.base + pm) >> gshift) << 8;
+                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + p) >> gshift) << 16;
+                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + pm) >> gshift) << 24;
+                }
+                pk[k] = w;
+            } else {
+                pk[k] = 0u;   // flat phase
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const float2 c0 = cs_lookup(cs, (pk[k] & 0xffu) << sh);
+            if constexpr (SINGLE) {
+                v[e0 + k] = make_float2(tp[k] * c0.x, tp[k] * c0.y);
+            } else {
+                const float2 c0m = cs_lookup(cs, ((pk[k] >> 8) & 0xffu) << sh);
+                const float2 c1 = cs_lookup(cs, ((pk[k] >> 16) & 0xffu) << sh);
+                const float2 c1m = cs_lookup(cs, (pk[k] >> 24) << sh);
+                // Hermitian parts E(k) + conj(E(-k)) of both sub-frames, packed as a + i b
+                const float2 h0 = make_float2(fmaf(tp[k], c0.x, tm[k] * c0m.x), fmaf(tp[k], c0.y, -tm[k] * c0m.y));
+                const float2 h1 = make_float2(fmaf(tp[k], c1.x, tm[k] * c1m.x), fmaf(tp[k], c1.y, -tm[k] * c1m.y));
+                v[e0 + k] = make_float2(h0.x - h1.y, h0.y + h1.x);
+            }
+        }
+    }
+}
+
 template <int NC>
 __global__ void __launch_bounds__((NC / ColCfg<NC>::R) * ColCfg<NC>::LPC)
 k_ospr_col_ifft(OsprArgs a) {
     constexpr int R = ColCfg<NC>::R, LPC = ColCfg<NC>::LPC, T = NC / R;
     extern __shared__ float2 sm[];
     float2* cs = sm;
-    float2* lines = sm + 256;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) cs[i] = a.cs256[i];
+    float2* lines = sm + kCsSmemEntries;
+    load_cs_table(cs, a.cs256);
     __syncthreads();
 
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
-    const int cm = (W - c) & (W - 1);
     const int s0 = 2 * (a.first_pair + int(blockIdx.y));
     const bool single = s0 + 1 >= a.N;
-    const SubframeDraw d0 = subframe_draw(a.ps, s0);
-    const SubframeDraw d1 = subframe_draw(a.ps, single ? s0 : s0 + 1);
-    const int sh = a.ps.cs_shift;
-
     float2 v[R];
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-        const int r = t + T * e;
-        const int rm = (NC - r) & (NC - 1);
-        const uint32_t p = uint32_t(r) * uint32_t(W) + uint32_t(c);
-        const uint32_t pm = uint32_t(rm) * uint32_t(W) + uint32_t(cm);
-        const float tp = __ldg(a.target + p);
-        const float2 c0 = cs[draw_code(a.ps, d0, p) << sh];
-        if (single) {
-            v[e] = make_float2(tp * c0.x, tp * c0.y);
-        } else {
-            const float tm = __ldg(a.target + pm);
-            const float2 c0m = cs[draw_code(a.ps, d0, pm) << sh];
-            const float2 c1 = cs[draw_code(a.ps, d1, p) << sh];
-            const float2 c1m = cs[draw_code(a.ps, d1, pm) << sh];
-            // Hermitian parts E(k) + conj(E(-k)) of both sub-frames, packed as a + i b
-            const float2 h0 = make_float2(fmaf(tp, c0.x, tm * c0m.x), fmaf(tp, c0.y, -tm * c0m.y));
-            const float2 h1 = make_float2(fmaf(tp, c1.x, tm * c1m.x), fmaf(tp, c1.y, -tm * c1m.y));
-            v[e] = make_float2(h0.x - h1.y, h0.y + h1.x);
-        }
+    if (a.ps.mode == kPhaseTable) {
+        if (single) ospr_build_column<NC, kPhaseTable, true>(v, a, cs, t, c, s0);
+        else ospr_build_column<NC, kPhaseTable, false>(v, a, cs, t, c, s0);
+    } else if (a.ps.mode == kPhaseGenerator) {
+        if (single) ospr_build_column<NC, kPhaseGenerator, true>(v, a, cs, t, c, s0);
+        else ospr_build_column<NC, kPhaseGenerator, false>(v, a, cs, t, c, s0);
+    } else {
+        if (single) ospr_build_column<NC, kPhaseFlat, true>(v, a, cs, t, c, s0);
+        else ospr_build_column<NC, kPhaseFlat, false>(v, a, cs, t, c, s0);
     }
-    line_fft<NC, R, +1, true>(v, lines + lc * line_stride(NC, R), t, a.tw);
+    line_fft<NC, R, +1, true>(v, lines + lc * col_stride<NC>(), t, a.tw);
     float2* z = a.zbuf + size_t(blockIdx.y) * size_t(NC) * size_t(W);
 #pragma unroll
     for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
@@ -174,7 +256,7 @@ __global__ void __launch_bounds__((NC / ColCfg<NC>::R) * ColCfg<NC>::LPC)
 k_ospr_col_fft(OsprArgs a) {
     constexpr int R = ColCfg<NC>::R, LPC = ColCfg<NC>::LPC, T = NC / R;
     extern __shared__ float2 sm[];
-    float2* lines = sm + 256;
+    float2* lines = sm;
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
@@ -187,7 +269,7 @@ k_ospr_col_fft(OsprArgs a) {
         float2 v[R];
 #pragma unroll
         for (int e = 0; e < R; ++e) v[e] = z[size_t(t + T * e) * W + c];
-        line_fft<NC, R, -1, true>(v, lines + lc * line_stride(NC, R), t, a.tw);
+        line_fft<NC, R, -1, true>(v, lines + lc * col_stride<NC>(), t, a.tw);
 #pragma unroll
         for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
     }
@@ -200,23 +282,30 @@ k_ospr_col_fft(OsprArgs a) {
 }
 
 // ---------------------------------------------------------------- finalize ----
+// I(k) = I(-k) = (sum_g S_g(k) + S_g(-k)) * scale: one thread per pixel pair {k, -k}
+// reads both accumulators once and writes both outputs. Thread q handles pixel q of the
+// first half of the raster (rows 0 .. H/2) whose mirror lies at or after it.
 __global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, int W,
                                 float scale, float* __restrict__ I) {
     const size_t P = size_t(H) * W;
+    const size_t half = P / 2 + W;             // rows 0 .. H/2 inclusive
     const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (p >= P) return;
+    if (p >= half) return;
     const int r = int(p / W), c = int(p % W);
     const size_t pm = size_t((H - r) & (H - 1)) * W + size_t((W - c) & (W - 1));
+    if (pm < p) return;                        // the pair was taken by its partner
     float s = 0.f;
     for (int g = 0; g < groups; ++g) s += S[size_t(g) * P + p] + S[size_t(g) * P + pm];
-    I[p] = s * scale;
+    s *= scale;
+    I[p] = s;
+    I[pm] = s;
 }
 
 // ------------------------------------------------------------------- host ----
 template <int NC>
 static int launch_col_ifft(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
-    constexpr size_t smem = col_smem_bytes<NC>();
+    constexpr size_t smem = col_ifft_smem_bytes<NC>();
     int rc = ensure_smem((const void*)k_ospr_col_ifft<NC>, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC>::LPC, a.pairs);
@@ -240,7 +329,7 @@ static int launch_row(const OsprArgs& a, cudaStream_t st) {
 template <int NC>
 static int launch_col_fft(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
-    constexpr size_t smem = col_smem_bytes<NC>();
+    constexpr size_t smem = col_fft_smem_bytes<NC>();
     int rc = ensure_smem((const void*)k_ospr_col_fft<NC>, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC>::LPC, a.groups);
@@ -282,12 +371,31 @@ struct OsprPlan {
     size_t z_bytes, s_bytes, total;
 };
 
+// Tuning override: HOLO_OSPR_CHUNK (pairs in flight, 1..16) and HOLO_OSPR_GROUPS
+// (partial accumulators, 1..4) replace the defaults; read once per process.
+static int env_int(const char* name, int lo, int hi, int dflt) {
+    const char* v = getenv(name);
+    if (!v || !*v) return dflt;
+    const int x = atoi(v);
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+static int tuned_chunk() {
+    static const int v = env_int("HOLO_OSPR_CHUNK", 1, kMaxChunkPairs, kMaxChunkPairs);
+    return v;
+}
+static int tuned_groups() {
+    static const int v = env_int("HOLO_OSPR_GROUPS", 1, kMaxGroups, kMaxGroups);
+    return v;
+}
+
 static OsprPlan ospr_plan(int H, int W, int N) {
     OsprPlan pl;
     const size_t P = size_t(H) * W;
     pl.npairs = (N + 1) / 2;
-    pl.chunk = pl.npairs < kMaxChunkPairs ? pl.npairs : kMaxChunkPairs;
-    pl.groups = pl.chunk < kMaxGroups ? pl.chunk : kMaxGroups;
+    const int cmax = tuned_chunk();
+    pl.chunk = pl.npairs < cmax ? pl.npairs : cmax;
+    const int gmax = tuned_groups();
+    pl.groups = pl.chunk < gmax ? pl.chunk : gmax;
     pl.z_bytes = align_up(size_t(pl.chunk) * P * sizeof(float2), 256);
     pl.s_bytes = align_up(size_t(pl.groups) * P * sizeof(float), 256);
     pl.total = pl.z_bytes + pl.s_bytes;
@@ -377,7 +485,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     if (replay) {
         const float scale = float(1.0 / (2.0 * double(N) * double(P)));
         const int threads = 256;
-        const int blocks = int((P + threads - 1) / threads);
+        const int blocks = int((P / 2 + W + threads - 1) / threads);
         Launch ln("ospr_finalize", st);
         k_ospr_finalize<<<blocks, threads, 0, st>>>(a.sacc, pl.groups, H, W, scale, d_replay);
         if ((rc = ln.done("ospr_finalize launch"))) return rc;
@@ -496,7 +604,7 @@ extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
     if (replay) {
         const float scale = float(1.0 / (2.0 * double(N) * double(P)));
         const int threads = 256;
-        const int blocks = int((P + threads - 1) / threads);
+        const int blocks = int((P / 2 + W + threads - 1) / threads);
         Launch ln("ospr_finalize", st);
         k_ospr_finalize<<<blocks, threads, 0, st>>>(a.sacc, pl.groups, H, W, scale, d_replay);
         if ((rc = ln.done("ospr_finalize launch"))) return rc;
