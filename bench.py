@@ -403,6 +403,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(name):
+    """Small fixed workloads for profiler captures (no timing, no JSON line)."""
+    import torch
+
+    from paper_2004_04049_gb300 import pipeline
+    from synthetic import blob_target
+
+    dev = torch.device("cuda:0")
+    if name == "frame":
+        # one 1024x1024 OSPR frame (N=24, L=10007), its replay error and 2 GS iterations, twice
+        T = torch.from_numpy(blob_target(H, W, 1000)).to(dev)
+        codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
+        for _ in range(2):
+            _, I = pipeline.ospr(T, N_SF, codes, GS_L)
+            e = pipeline.error(I, T)
+            pipeline.gs(T, 2, 256, codes, GS_L, 256, LUT_SEED)
+        torch.cuda.synchronize()
+        print("case frame ok, nmse", float(e[2]))
+    else:
+        raise SystemExit(f"unknown case {name!r}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,7 +433,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--case", default=None, help="run a small fixed workload for a profiler capture")
     args = ap.parse_args()
+    if args.case:
+        from paper_2004_04049_gb300 import build_lib
+        build_lib.build()
+        run_case(args.case)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
