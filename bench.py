@@ -305,6 +305,8 @@ def run_ours(args):
     e2e_value = world * subframes_per_step * e2e_steps / (e2e_ms / 1e3)
     nmse = errs[:, 2].cpu().numpy()
 
+    batch = run_batch_leg(dev, stream) if not args.no_batch else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(seconds=args.cpu_seconds)
@@ -332,6 +334,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "sub-frames/s",
                     "h2d_bytes_per_step": len(L_SWEEP) * 4 * P,
                     "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 4 * P + 24)},
+            "batch": batch,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -339,6 +342,81 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------ mixed-shape batch leg ----
+BATCH_SHAPES = [(512, 512), (1024, 1024), (2048, 2048), (1024, 2048)]
+
+
+def batch_frames(n_frames=64, seed=42):
+    """The mixed-shape batch: shape uniform over BATCH_SHAPES, N uniform in 8..32,
+    L = 2^k with k uniform in 10..18, blob targets; table seed = base seed + frame."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for f in range(n_frames):
+        H, W = BATCH_SHAPES[int(rng.integers(0, len(BATCH_SHAPES)))]
+        N = int(rng.integers(8, 33))
+        L = 1 << int(rng.integers(10, 19))
+        out.append((H, W, N, L, seed + f))
+    return out
+
+
+def run_batch_leg(dev, stream, reps=3):
+    import torch
+
+    from paper_2004_04049_gb300 import holo, pipeline
+    from synthetic import blob_target
+
+    frames = batch_frames()
+    bufs = []
+    descs = []
+    for k, (H, W, N, L, seed) in enumerate(frames):
+        b = {"T": torch.from_numpy(blob_target(H, W, 3000 + k)).to(dev),
+             "codes": torch.empty(L, dtype=torch.uint8, device=dev),
+             "bits": torch.empty((N, H * W // 32), dtype=torch.int32, device=dev),
+             "I": torch.empty((H, W), dtype=torch.float32, device=dev),
+             "err": torch.empty(3, dtype=torch.float64, device=dev)}
+        bufs.append(b)
+        descs.append(holo.frame_desc(b["T"], H, W, N, b["codes"], L, 256, seed, True, 0, 0,
+                                     b["bits"], b["I"], b["err"]))
+    arr = holo.frame_array(descs)
+    ws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=dev)
+    sub = sum(f[2] for f in frames)
+    s = stream.cuda_stream
+
+    def per_frame():
+        for (H, W, N, L, seed), b in zip(frames, bufs):
+            holo.lut_build(seed, L, 256, b["codes"], None, stream=s)
+            pipeline.ospr(b["T"], N, b["codes"], L, 256, seed, ws=ws, out_bits=b["bits"], out_replay=b["I"],
+                          stream=s)
+            pipeline.error(b["I"], b["T"], out=b["err"], stream=s)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        ms = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    t_pf = timed(per_frame)
+    t_batch = timed(lambda: holo.ospr_generate_batch(arr, holo.HOLO_FP32, ws, stream=s))
+    g = holo.ospr_batch_graph_create(arr, holo.HOLO_FP32, ws)
+    try:
+        t_graph = timed(lambda: holo.holo_graph_launch(g, s))
+    finally:
+        holo.holo_graph_destroy(g)
+    return {"workload": "64 frames, shapes {512^2, 1024^2, 2048^2, 1024x2048}, N in 8..32, L = 2^(10..18), "
+                        "seed 42, blob targets; per frame lut_build + ospr_generate + replay_error",
+            "subframes": sub, "unit": "sub-frames/s",
+            "per_frame_launches": sub / (t_pf / 1e3), "batch_call": sub / (t_batch / 1e3),
+            "graph_launch": sub / (t_graph / 1e3), "ms": {"per_frame": t_pf, "batch": t_batch, "graph": t_graph}}
 
 
 # ------------------------------------------------------------- CPU oracle arm ----
@@ -432,6 +510,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-shape batch leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--case", default=None, help="run a small fixed workload for a profiler capture")
     args = ap.parse_args()

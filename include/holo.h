@@ -181,6 +181,66 @@ int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
                           int64_t start_index, int64_t subframe_stride, int precision,
                           uint32_t* d_holo_bits, float* d_replay, holo_stream_t s);
 
+/* ------------------------------------------------------- batched frames ---- */
+
+/*
+ * A batch of independent OSPR frames of mixed shapes, each with its own table and
+ * sub-frame count (Section 5, Fig. 3: frames draw from the pool; here each frame may also
+ * build its own table first). Field meanings follow ospr_generate and lut_build.
+ *   d_codes    [L] uint8: filled by lut_build(seed, L, levels) first when build_lut != 0,
+ *              otherwise read as given.
+ *   d_err      [3] float64 (alpha, mse, nmse of the replay, as replay_error) or NULL;
+ *              needs d_replay.
+ */
+typedef struct holo_frame_desc {
+    const float* d_target;
+    int H, W, N;
+    uint8_t* d_codes;
+    int64_t L;
+    int levels;
+    uint64_t seed;
+    int build_lut;
+    int64_t start_index;
+    int64_t subframe_stride;
+    uint32_t* d_holo_bits;
+    float* d_replay;
+    double* d_err;
+} holo_frame_desc;
+
+/*
+ * ospr_batch_workspace_size - bytes of device workspace ospr_generate_batch (and the
+ * graph made by ospr_batch_graph_create) needs for these frames.
+ */
+int ospr_batch_workspace_size(const holo_frame_desc* h_frames, int n_frames, int precision,
+                              size_t* bytes);
+
+/*
+ * ospr_generate_batch - runs every frame of the batch (lut_build if asked, ospr_generate,
+ * replay_error if d_err is given) with frames spread over the library's internal streams
+ * so that frames of different shapes share the GPU. Frames are assigned longest first to
+ * the least-loaded of S streams (S = 8, environment override HOLO_BATCH_STREAMS=1..32);
+ * each stream's frames run in order on that stream's slice of the workspace. The call
+ * forks from and joins back to stream `s`: work queued on `s` before the call runs first,
+ * work queued after it waits for every frame. Results equal those of per-frame calls.
+ *   h_frames   host array of n_frames descriptors (read during the call only).
+ * Errors: as the per-frame calls, with the index of the offending frame in the message.
+ */
+int ospr_generate_batch(const holo_frame_desc* h_frames, int n_frames, int precision,
+                        void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/*
+ * A CUDA graph of a whole batch: ospr_batch_graph_create runs the batch once on a private
+ * stream (to finish every lazy set-up), then captures it into an executable graph, so
+ * that one holo_graph_launch replays the whole batch with a single launch. The graph
+ * keeps the descriptors' pointers: refill the same buffers between launches. Launches of
+ * one graph must not overlap (they share the workspace).
+ */
+typedef struct holo_graph holo_graph;
+int ospr_batch_graph_create(const holo_frame_desc* h_frames, int n_frames, int precision,
+                            void* d_ws, size_t ws_bytes, holo_graph** out);
+int holo_graph_launch(holo_graph* g, holo_stream_t s);
+int holo_graph_destroy(holo_graph* g);
+
 /* --------------------------------------------------------------------- GS ---- */
 
 /*

@@ -98,6 +98,8 @@ int Launch::done(const char* what) {
     return HOLO_OK;
 }
 
+int profiling_swap(int on) { return g_profiling.exchange(on ? 1 : 0); }
+
 static int collect_locked() {
     for (auto& kv : g_prof) {
         FamilyStats& fs = kv.second;

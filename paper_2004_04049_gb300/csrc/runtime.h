@@ -34,6 +34,9 @@ class Launch {
     cudaEvent_t start_ = nullptr;
 };
 
+// Sets event profiling on or off and returns the previous setting.
+int profiling_swap(int on);
+
 // ---- constant tables ---------------------------------------------------------
 struct Tables {
     const float2* twiddles;   // Stockham stage twiddles, see fft_core.cuh

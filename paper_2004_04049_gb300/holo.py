@@ -38,6 +38,26 @@ class HoloError(RuntimeError):
 _lib = None
 
 _c = ctypes
+
+
+class FrameDesc(ctypes.Structure):
+    """holo_frame_desc of include/holo.h (same field order and C layout)."""
+    _fields_ = [("d_target", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int),
+                ("d_codes", ctypes.c_void_p), ("L", ctypes.c_int64), ("levels", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("build_lut", ctypes.c_int), ("start_index", ctypes.c_int64),
+                ("subframe_stride", ctypes.c_int64), ("d_holo_bits", ctypes.c_void_p),
+                ("d_replay", ctypes.c_void_p), ("d_err", ctypes.c_void_p)]
+
+
+def frame_desc(d_target, H, W, N, d_codes=None, L=0, levels=256, seed=0, build_lut=False, start_index=0,
+               subframe_stride=0, d_holo_bits=None, d_replay=None, d_err=None):
+    return FrameDesc(_ptr(d_target), H, W, N, _ptr(d_codes), L, levels, seed, 1 if build_lut else 0,
+                     start_index, subframe_stride, _ptr(d_holo_bits), _ptr(d_replay), _ptr(d_err))
+
+
+def frame_array(descs):
+    arr = (FrameDesc * len(descs))(*descs)
+    return arr
 _SIGS = {
     "holo_version": (_c.c_int, []),
     "holo_last_error": (_c.c_char_p, []),
@@ -56,6 +76,12 @@ _SIGS = {
                                          _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
                                          _c.c_int64, _c.c_int64, _c.c_int,
                                          _c.c_void_p, _c.c_void_p, _c.c_void_p]),
+    "ospr_batch_workspace_size": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "ospr_generate_batch": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "ospr_batch_graph_create": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
+                                           _c.POINTER(_c.c_void_p)]),
+    "holo_graph_launch": (_c.c_int, [_c.c_void_p, _c.c_void_p]),
+    "holo_graph_destroy": (_c.c_int, [_c.c_void_p]),
     "gs_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "gs_iterate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
                               _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
@@ -185,6 +211,43 @@ def ospr_generate_noalloc(d_target, H, W, N, d_codes, L, levels, seed, start_ind
     return _call("ospr_generate_noalloc", _ptr(d_target), H, W, N, _ptr(d_codes), L, levels, seed,
                  start_index, subframe_stride, precision, _ptr(d_holo_bits), _ptr(d_replay),
                  _stream(stream, d_target))
+
+
+def ospr_batch_workspace_size(frames, precision=HOLO_FP32):
+    """frames: a ctypes array made by frame_array()."""
+    b = ctypes.c_size_t(0)
+    _call("ospr_batch_workspace_size", ctypes.cast(frames, ctypes.c_void_p), len(frames), precision,
+          ctypes.byref(b))
+    return b.value
+
+
+def ospr_generate_batch(frames, precision, d_ws, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("ospr_generate_batch", ctypes.cast(frames, ctypes.c_void_p), len(frames), precision,
+                 _ptr(d_ws), ws_bytes, _stream(stream, d_ws))
+
+
+def ospr_batch_graph_create(frames, precision, d_ws, ws_bytes=None):
+    """Returns an opaque graph handle (int)."""
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    g = ctypes.c_void_p(0)
+    _call("ospr_batch_graph_create", ctypes.cast(frames, ctypes.c_void_p), len(frames), precision,
+          _ptr(d_ws), ws_bytes, ctypes.byref(g))
+    return g.value
+
+
+def holo_graph_launch(graph, stream=None):
+    s = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else None)
+    if s is None:
+        import torch
+        s = torch.cuda.current_stream().cuda_stream
+    return _call("holo_graph_launch", graph, s)
+
+
+def holo_graph_destroy(graph):
+    return _call("holo_graph_destroy", graph)
 
 
 def gs_workspace_size(H, W, iters, precision=HOLO_FP32):

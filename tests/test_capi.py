@@ -75,3 +75,15 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert rc == holo.HOLO_EINVAL
     n = ctypes.c_uint64(0)
     assert lib.holo_launch_count(ctypes.byref(n)) == 0
+
+
+def test_batch_workspace_is_host_only(lib):
+    fr = [holo.frame_desc(1 << 20, 512, 512, 9, 1 << 21, 1031, 256, 1, True, 0, 0, 1 << 22, 1 << 23, 1 << 24),
+          holo.frame_desc(1 << 20, 1024, 2048, 30, 1 << 21, 4096, 256, 2, True, 0, 0, 1 << 22, 1 << 23, None)]
+    arr = holo.frame_array(fr)
+    total = holo.ospr_batch_workspace_size(arr)
+    assert total >= 2 * holo.ospr_workspace_size(1024, 2048, 30)
+    bad = holo.frame_array([holo.frame_desc(1 << 20, 96, 512, 9, None, 0, 256, 0, False, 0, 0, 1 << 22, None, None)])
+    with pytest.raises(holo.HoloError) as ei:
+        holo.ospr_batch_workspace_size(bad)
+    assert "frame 0" in str(ei.value)

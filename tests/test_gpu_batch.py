@@ -1,0 +1,101 @@
+"""ospr_generate_batch and its CUDA graph: a batch of mixed-shape frames, each with its
+own table, gives exactly the per-frame results (the same kernels run per frame, only
+spread over internal streams), as a direct call and as a replayed graph."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2004_04049_gb300 import holo, pipeline
+from synthetic import blob_target, noise_target
+
+pytestmark = pytest.mark.gpu
+
+FRAMES = [  # H, W, N, L, seed
+    (128, 128, 5, 1031, 11),
+    (256, 512, 8, 4099, 12),
+    (64, 64, 1, 0, 13),
+    (512, 256, 3, holo.L_UNREPEATED, 14),
+    (1024, 1024, 6, 10007, 15),
+    (256, 256, 32, 65537, 16),
+]
+
+
+def _alloc(cuda, spec, k):
+    H, W, N, L, seed = spec
+    T = blob_target(H, W, 1100 + k) if k % 2 == 0 else noise_target(H, W, 2100 + k)
+    return {
+        "T": torch.from_numpy(T).to(cuda),
+        "codes": torch.zeros(max(L, 1), dtype=torch.uint8, device=cuda),
+        "bits": torch.zeros((N, H * W // 32), dtype=torch.int32, device=cuda),
+        "I": torch.zeros((H, W), dtype=torch.float32, device=cuda),
+        "err": torch.zeros(3, dtype=torch.float64, device=cuda),
+    }
+
+
+def _descs(bufs):
+    out = []
+    for (H, W, N, L, seed), b in zip(FRAMES, bufs):
+        out.append(holo.frame_desc(b["T"], H, W, N, b["codes"], L, 256, seed, L > 0, 0, 0,
+                                   b["bits"], b["I"], b["err"]))
+    return holo.frame_array(out)
+
+
+def _per_frame(cuda, bufs):
+    ref = []
+    for (H, W, N, L, seed), b in zip(FRAMES, bufs):
+        codes = pipeline.lut(seed, L, device=cuda) if L > 0 else None
+        bits, I = pipeline.ospr(b["T"], N, codes, L, 256, seed)
+        err = pipeline.error(I, b["T"])
+        ref.append((bits.cpu().numpy(), I.cpu().numpy(), err.cpu().numpy()))
+    return ref
+
+
+def _check(bufs, ref):
+    for k, (b, r) in enumerate(zip(bufs, ref)):
+        assert np.array_equal(b["bits"].cpu().numpy(), r[0]), k
+        assert np.array_equal(b["I"].cpu().numpy(), r[1]), k
+        assert np.array_equal(b["err"].cpu().numpy(), r[2]), k
+
+
+def test_batch_equals_per_frame(cuda):
+    bufs = [_alloc(cuda, s, k) for k, s in enumerate(FRAMES)]
+    arr = _descs(bufs)
+    ws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=cuda)
+    holo.ospr_generate_batch(arr, holo.HOLO_FP32, ws)
+    torch.cuda.synchronize()
+    _check(bufs, _per_frame(cuda, bufs))
+
+
+def test_graph_replays_batch(cuda):
+    bufs = [_alloc(cuda, s, k) for k, s in enumerate(FRAMES)]
+    arr = _descs(bufs)
+    ws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=cuda)
+    g = holo.ospr_batch_graph_create(arr, holo.HOLO_FP32, ws)
+    try:
+        for b in bufs:
+            b["I"].zero_()
+            b["bits"].zero_()
+        holo.holo_graph_launch(g)
+        torch.cuda.synchronize()
+        _check(bufs, _per_frame(cuda, bufs))
+        # new target contents in the same buffers: the replay follows them
+        for k, b in enumerate(bufs):
+            b["T"].copy_(torch.flip(b["T"], dims=[0]))
+        holo.holo_graph_launch(g)
+        torch.cuda.synchronize()
+        _check(bufs, _per_frame(cuda, bufs))
+    finally:
+        holo.holo_graph_destroy(g)
+
+
+def test_batch_reports_bad_frame(cuda):
+    bufs = [_alloc(cuda, s, k) for k, s in enumerate(FRAMES[:2])]
+    descs = [holo.frame_desc(bufs[0]["T"], 128, 128, 5, bufs[0]["codes"], 1031, 256, 1, True, 0, 0,
+                             bufs[0]["bits"], bufs[0]["I"], None),
+             holo.frame_desc(bufs[1]["T"], 100, 512, 8, None, 0, 256, 1, False, 0, 0,
+                             bufs[1]["bits"], bufs[1]["I"], None)]
+    arr = holo.frame_array(descs)
+    with pytest.raises(holo.HoloError) as ei:
+        holo.ospr_batch_workspace_size(arr)
+    assert "frame 1" in str(ei.value)
