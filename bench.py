@@ -166,7 +166,6 @@ def run_ours(args):
                torch.from_numpy(noise_target(H, W, 2000 + rank)).to(dev)]
     maxL = max(L_SWEEP)
     codes = torch.empty(maxL, dtype=torch.uint8, device=dev)
-    ws = torch.empty(holo.ospr_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
     ews = torch.empty(holo.replay_error_workspace_size(H, W), dtype=torch.uint8, device=dev)
     bits = torch.empty((N_SF, P // 32), dtype=torch.int32, device=dev)
     replay = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -188,6 +187,11 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
+
+    # FFT tile variants and chunking for this shape, picked by the library's autotuner
+    tune_ms = holo.ospr_autotune(H, W, N_SF, reps=3, stream=stream.cuda_stream) if not args.no_tune else None
+    tuning = holo.ospr_tuning_get(H, W)
+    ws = torch.empty(holo.ospr_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
 
     for _ in range(args.warmup):
         step()
@@ -225,8 +229,8 @@ def run_ours(args):
             "err_pass2", "err_finish"]
     prof = {f: holo.holo_profile_read(f) for f in fams}
     npairs = (N_SF + 1) // 2
-    chunk = min(npairs, int(os.environ.get("HOLO_OSPR_CHUNK", "16")))
-    groups = min(chunk, int(os.environ.get("HOLO_OSPR_GROUPS", "4")))
+    chunk = min(npairs, tuning["chunk"])
+    groups = min(chunk, tuning["groups"])
     dom = max(fams, key=lambda f: prof[f][1])
     n_dom, ms_dom = prof[dom]
     peaks = _peaks()
@@ -319,6 +323,7 @@ def run_ours(args):
             "value": value, "unit": "sub-frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "tuning": dict(tuning, autotune_ms_per_frame=tune_ms),
             "config": {"workload": "ospr_1024x1024_N24_Lsweep", "H": H, "W": W, "N": N_SF,
                        "L": "2^8..2^20 + unrepeated", "frames_per_step": len(L_SWEEP),
                        "targets": "seeded blob / band-limited noise", "l2": "flushed before each step",
@@ -368,6 +373,10 @@ def run_batch_leg(dev, stream, reps=3):
     from synthetic import blob_target
 
     frames = batch_frames()
+    tunings = {}
+    for (H_, W_) in BATCH_SHAPES:
+        holo.ospr_autotune(H_, W_, 24, reps=2, stream=stream.cuda_stream)
+        tunings[f"{H_}x{W_}"] = holo.ospr_tuning_get(H_, W_)
     bufs = []
     descs = []
     for k, (H, W, N, L, seed) in enumerate(frames):
@@ -416,7 +425,8 @@ def run_batch_leg(dev, stream, reps=3):
                         "seed 42, blob targets; per frame lut_build + ospr_generate + replay_error",
             "subframes": sub, "unit": "sub-frames/s",
             "per_frame_launches": sub / (t_pf / 1e3), "batch_call": sub / (t_batch / 1e3),
-            "graph_launch": sub / (t_graph / 1e3), "ms": {"per_frame": t_pf, "batch": t_batch, "graph": t_graph}}
+            "graph_launch": sub / (t_graph / 1e3), "ms": {"per_frame": t_pf, "batch": t_batch, "graph": t_graph},
+            "tuning": tunings}
 
 
 # ------------------------------------------------------------- CPU oracle arm ----
@@ -511,6 +521,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-shape batch leg")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default FFT tiles and chunking")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--case", default=None, help="run a small fixed workload for a profiler capture")
     args = ap.parse_args()

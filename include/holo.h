@@ -136,9 +136,10 @@ int ospr_workspace_size(int H, int W, int N, int precision, size_t* bytes);
  *   d_replay     [H][W] float32 output or NULL: mean replay intensity over sub-frames.
  *   d_ws         device workspace of at least ospr_workspace_size() bytes, 256-byte
  *                aligned. Sub-frame pairs go through the transforms in chunks of up to
- *                16 pairs (environment override HOLO_OSPR_CHUNK=1..16, read once per
- *                process; HOLO_OSPR_GROUPS=1..4 sets the partial accumulators); the
- *                workspace size follows the same setting.
+ *                16 pairs; the chunk size, accumulator groups and FFT tile variants come
+ *                from the shape's tuning (ospr_autotune / ospr_tuning_set; defaults
+ *                overridable with HOLO_OSPR_CHUNK=1..16 and HOLO_OSPR_GROUPS=1..4), and
+ *                the workspace size follows the same setting.
  * Design-rule warnings (Section 8: L prime, L > N, L > max(H, W)) are returned with
  * HOLO_OK and a message in holo_last_error(). Errors: HOLO_EINVAL, HOLO_EUNSUPPORTED,
  * HOLO_EWORKSPACE, HOLO_ECUDA.
@@ -148,6 +149,25 @@ int ospr_generate(const float* d_target, int H, int W, int N,
                   int64_t start_index, int64_t subframe_stride, int precision,
                   uint32_t* d_holo_bits, float* d_replay,
                   void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/*
+ * OSPR tuning per shape (H, W): the tile variant of the column passes and of the row pass
+ * (0 or 1; lengths below 512 have only variant 0), the sub-frame pairs in flight per
+ * chunk (1..16) and the partial accumulators of the column DFT pass (1..4). Every
+ * setting computes the same values up to float32 rounding order; the workspace size of
+ * ospr_workspace_size follows the current setting, so query it after changing it.
+ * ospr_autotune times ospr_generate on synthetic data of this shape (a 10007-entry table)
+ * for candidate settings (coordinate descent: column variant, row variant, chunk, groups;
+ * each the median of `reps` runs after one warm-up, CUDA events on stream s), installs the
+ * fastest for this process and, when the environment variable HOLO_TUNE_CACHE names a
+ * file, writes every installed setting there (one JSON object per line), from where later
+ * processes read it. It allocates and frees its own scratch (HOLO_ENOMEM if that fails)
+ * and synchronises s. best_ms (nullable) receives the winner's time per call.
+ * ospr_tuning_set installs a setting without timing (for tests and reproduction).
+ */
+int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, double* best_ms);
+int ospr_tuning_get(int H, int W, int* col_variant, int* row_variant, int* chunk, int* groups);
+int ospr_tuning_set(int H, int W, int col_variant, int row_variant, int chunk, int groups);
 
 /*
  * ospr_generate_noalloc - ospr_generate for callers that cannot allocate device memory.

@@ -20,266 +20,16 @@
 //   row       rows:    row IDFT, binarise (bits out), row DFT of h_{s0} + i h_{s1}
 //   col_fft   columns: column DFT, S += |Z|^2 over the pairs of a group
 // then finalize: I(k) = (sum_g S_g(k) + S_g(-k)) / (2*N*H*W).
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
+#include <map>
 #include <mutex>
 
-#include "fft_core.cuh"
-#include "phase_source.cuh"
-#include "runtime.h"
+#include "ospr_kernels.cuh"
 
 namespace holo {
-
-// launch shapes per line length: column passes hold LPC columns of R-element threads
-template <int N> struct ColCfg;
-template <> struct ColCfg<64>   { static constexpr int R = 8,  LPC = 32; };
-template <> struct ColCfg<128>  { static constexpr int R = 16, LPC = 32; };
-template <> struct ColCfg<256>  { static constexpr int R = 16, LPC = 32; };
-template <> struct ColCfg<512>  { static constexpr int R = 16, LPC = 16; };
-template <> struct ColCfg<1024> { static constexpr int R = 32, LPC = 16; };
-template <> struct ColCfg<2048> { static constexpr int R = 32, LPC = 8; };
-template <> struct ColCfg<4096> { static constexpr int R = 32, LPC = 4; };
-// row passes: T = N/R >= 32 threads per row so that a warp holds 32 consecutive pixels
-template <int N> struct RowCfg;
-template <> struct RowCfg<64>   { static constexpr int R = 2,  LPR = 4; };
-template <> struct RowCfg<128>  { static constexpr int R = 4,  LPR = 4; };
-template <> struct RowCfg<256>  { static constexpr int R = 8,  LPR = 4; };
-template <> struct RowCfg<512>  { static constexpr int R = 16, LPR = 4; };
-template <> struct RowCfg<1024> { static constexpr int R = 32, LPR = 4; };
-template <> struct RowCfg<2048> { static constexpr int R = 32, LPR = 2; };
-template <> struct RowCfg<4096> { static constexpr int R = 32, LPR = 1; };
-
-constexpr int kMaxChunkPairs = 16;   // pairs whose fields are in flight at once
-constexpr int kMaxGroups = 4;        // partial accumulators of the column DFT pass
-
-struct OsprArgs {
-    const float* target;
-    int H, W, N;
-    PhaseSource ps;
-    float2* zbuf;         // [chunk pairs][H][W]
-    float* sacc;          // [groups][H][W]
-    int groups;
-    int first_pair;       // global index of the chunk's pair 0
-    int pairs;            // pairs in this chunk
-    uint32_t* bits;       // [N][H*W/32] or null
-    int accumulate;       // add to sacc instead of overwriting
-    const float2* tw;
-    const float2* cs256;
-};
-
-template <int NC>
-constexpr int col_stride() { return col_line_stride(NC, ColCfg<NC>::R, ColCfg<NC>::LPC); }
-// pass 1 also holds the replicated cos/sin table
-template <int NC>
-constexpr size_t col_ifft_smem_bytes() {
-    return sizeof(float2) * (kCsSmemEntries + size_t(ColCfg<NC>::LPC) * col_stride<NC>());
-}
-template <int NC>
-constexpr size_t col_fft_smem_bytes() {
-    return sizeof(float2) * size_t(ColCfg<NC>::LPC) * col_stride<NC>();
-}
-template <int NR>
-constexpr size_t row_smem_bytes() {
-    return sizeof(float2) * size_t(RowCfg<NR>::LPR) * line_stride(NR, RowCfg<NR>::R);
-}
-
-// ------------------------------------------------------------------ pass 1 ----
-// Z for one column of one pair, in canonical layout (slot e <-> row t + T*e). MODE and
-// SINGLE are compile-time so that the element loops hold no branches: for each batch of
-// kBatch elements every load (target, mirror target, four codes) is issued before any
-// of them is used.
-constexpr int kBatch = 8;
-
-template <int NC, int MODE, bool SINGLE>
-__device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC>::R], const OsprArgs& a,
-                                                  const float2* cs, int t, int c, int s0) {
-    constexpr int R = ColCfg<NC>::R, T = NC / R;
-    constexpr int B = R < kBatch ? R : kBatch;
-    const int W = a.W;
-    const int cm = (W - c) & (W - 1);
-    const int sh = a.ps.cs_shift;
-    const SubframeDraw d0 = subframe_draw(a.ps, s0);
-    const SubframeDraw d1 = subframe_draw(a.ps, SINGLE ? s0 : s0 + 1);
-    // table mode: indices (start + s*stride + p) mod L advance by D = T*W mod L per element;
-    // the mirror pixel of row r = t + T*e is (H - r)*W + cm = q0 - e*T*W, except for row 0
-    const uint32_t L = a.ps.L;
-    const uint64_t fm = a.ps.fm;
-    uint32_t D = 0, i0 = 0, i1 = 0, m0 = 0, m1 = 0, z0 = 0, z1 = 0;
-    if constexpr (MODE == kPhaseTable) {
-        D = uint32_t((uint64_t(T) * uint64_t(W)) % L);
-        const uint32_t p0 = uint32_t(t) * uint32_t(W) + uint32_t(c);
-        const uint32_t q0 = uint32_t(NC - t) * uint32_t(W) + uint32_t(cm);
-        i0 = fastmod_u32(d0.base_mod + p0, fm, L);
-        i1 = fastmod_u32(d1.base_mod + p0, fm, L);
-        m0 = fastmod_u32(d0.base_mod + q0, fm, L);
-        m1 = fastmod_u32(d1.base_mod + q0, fm, L);
-        z0 = fastmod_u32(d0.base_mod + uint32_t(cm), fm, L);
-        z1 = fastmod_u32(d1.base_mod + uint32_t(cm), fm, L);
-    }
-    const int gshift = 64 - a.ps.bits;
-#pragma unroll
-    for (int e0 = 0; e0 < R; e0 += B) {
-        float tp[B], tm[B];
-        uint32_t pk[B];   // codes of (s0, p), (s0, -p), (s1, p), (s1, -p), one byte each
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-            const int e = e0 + k;
-            const int r = t + T * e;
-            const int rm = (NC - r) & (NC - 1);
-            tp[k] = __ldg(a.target + r * W + c);
-            tm[k] = SINGLE ? 0.f : __ldg(a.target + rm * W + cm);
-            if constexpr (MODE == kPhaseTable) {
-                const uint32_t jm0 = (e == 0 && t == 0) ? z0 : m0;
-                const uint32_t jm1 = (e == 0 && t == 0) ? z1 : m1;
-                uint32_t w = __ldg(a.ps.codes + i0);
-                if constexpr (!SINGLE) {
-                    w |= uint32_t(__ldg(a.ps.codes + jm0)) << 8;
-                    w |= uint32_t(__ldg(a.ps.codes + i1)) << 16;
-                    w |= uint32_t(__ldg(a.ps.codes + jm1)) << 24;
-                }
-                pk[k] = w;
-                i0 += D; i0 -= (i0 >= L) ? L : 0u;
-                i1 += D; i1 -= (i1 >= L) ? L : 0u;
-                m0 = (m0 >= D) ? m0 - D : m0 + (L - D);
-                m1 = (m1 >= D) ? m1 - D : m1 + (L - D);
-            } else if constexpr (MODE == kPhaseGenerator) {
-                const uint64_t p = uint64_t(r) * uint64_t(W) + uint64_t(c);
-                const uint64_t pm = uint64_t(rm) * uint64_t(W) + uint64_t(cm);
-                uint32_t w = uint32_t(splitmix64_at(a.ps.seed, d0.base + p) >> gshift);
-                if constexpr (!SINGLE) {
-                    w |= uint32_t(splitmix64_at(a.ps.seed, d0.base + pm) >> gshift) << 8;
-                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + p) >> gshift) << 16;
-                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + pm) >> gshift) << 24;
-                }
-                pk[k] = w;
-            } else {
-                pk[k] = 0u;   // flat phase
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-            const float2 c0 = cs_lookup(cs, (pk[k] & 0xffu) << sh);
-            if constexpr (SINGLE) {
-                v[e0 + k] = make_float2(tp[k] * c0.x, tp[k] * c0.y);
-            } else {
-                const float2 c0m = cs_lookup(cs, ((pk[k] >> 8) & 0xffu) << sh);
-                const float2 c1 = cs_lookup(cs, ((pk[k] >> 16) & 0xffu) << sh);
-                const float2 c1m = cs_lookup(cs, (pk[k] >> 24) << sh);
-                // Hermitian parts E(k) + conj(E(-k)) of both sub-frames, packed as a + i b
-                const float2 h0 = make_float2(fmaf(tp[k], c0.x, tm[k] * c0m.x), fmaf(tp[k], c0.y, -tm[k] * c0m.y));
-                const float2 h1 = make_float2(fmaf(tp[k], c1.x, tm[k] * c1m.x), fmaf(tp[k], c1.y, -tm[k] * c1m.y));
-                v[e0 + k] = make_float2(h0.x - h1.y, h0.y + h1.x);
-            }
-        }
-    }
-}
-
-template <int NC>
-__global__ void __launch_bounds__((NC / ColCfg<NC>::R) * ColCfg<NC>::LPC)
-k_ospr_col_ifft(OsprArgs a) {
-    constexpr int R = ColCfg<NC>::R, LPC = ColCfg<NC>::LPC, T = NC / R;
-    extern __shared__ float2 sm[];
-    float2* cs = sm;
-    float2* lines = sm + kCsSmemEntries;
-    load_cs_table(cs, a.cs256);
-    __syncthreads();
-
-    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
-    const int W = a.W;
-    const int c = blockIdx.x * LPC + lc;
-    const int s0 = 2 * (a.first_pair + int(blockIdx.y));
-    const bool single = s0 + 1 >= a.N;
-    float2 v[R];
-    if (a.ps.mode == kPhaseTable) {
-        if (single) ospr_build_column<NC, kPhaseTable, true>(v, a, cs, t, c, s0);
-        else ospr_build_column<NC, kPhaseTable, false>(v, a, cs, t, c, s0);
-    } else if (a.ps.mode == kPhaseGenerator) {
-        if (single) ospr_build_column<NC, kPhaseGenerator, true>(v, a, cs, t, c, s0);
-        else ospr_build_column<NC, kPhaseGenerator, false>(v, a, cs, t, c, s0);
-    } else {
-        if (single) ospr_build_column<NC, kPhaseFlat, true>(v, a, cs, t, c, s0);
-        else ospr_build_column<NC, kPhaseFlat, false>(v, a, cs, t, c, s0);
-    }
-    line_fft<NC, R, +1, true>(v, lines + lc * col_stride<NC>(), t, a.tw);
-    float2* z = a.zbuf + size_t(blockIdx.y) * size_t(NC) * size_t(W);
-#pragma unroll
-    for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
-}
-
-// ------------------------------------------------------------------ pass 2 ----
-template <int NR, bool REPLAY>
-__global__ void __launch_bounds__((NR / RowCfg<NR>::R) * RowCfg<NR>::LPR)
-k_ospr_row(OsprArgs a) {
-    constexpr int R = RowCfg<NR>::R, T = NR / R;
-    constexpr bool BLOCK = T > 32;
-    extern __shared__ float2 sm[];
-    const int line = threadIdx.x / T, t = threadIdx.x % T;
-    const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * RowCfg<NR>::LPR + line;
-    const int s0 = 2 * (a.first_pair + int(blockIdx.y));
-    const bool single = s0 + 1 >= a.N;
-    const size_t P = size_t(a.H) * NR;
-    float2* z = a.zbuf + size_t(blockIdx.y) * P + size_t(r) * NR;
-    float2* buf = sm + line * line_stride(NR, R);
-
-    float2 v[R];
-#pragma unroll
-    for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
-    line_fft<NR, R, +1, BLOCK>(v, buf, t, a.tw);
-
-    const size_t words = P / 32;
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-        const bool n0 = v[e].x < 0.f;
-        const bool n1 = v[e].y < 0.f;
-        if (a.bits) {
-            const unsigned b0 = __ballot_sync(0xffffffffu, n0);
-            const unsigned b1 = __ballot_sync(0xffffffffu, n1);
-            if (lane == 0) {
-                const size_t w = (size_t(r) * NR + size_t(t - lane + T * e)) >> 5;
-                a.bits[size_t(s0) * words + w] = b0;
-                if (!single) a.bits[size_t(s0 + 1) * words + w] = b1;
-            }
-        }
-        v[e] = make_float2(n0 ? -1.f : 1.f, single ? 0.f : (n1 ? -1.f : 1.f));
-    }
-    if constexpr (REPLAY) {
-        line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
-#pragma unroll
-        for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
-    }
-}
-
-// ------------------------------------------------------------------ pass 3 ----
-template <int NC>
-__global__ void __launch_bounds__((NC / ColCfg<NC>::R) * ColCfg<NC>::LPC)
-k_ospr_col_fft(OsprArgs a) {
-    constexpr int R = ColCfg<NC>::R, LPC = ColCfg<NC>::LPC, T = NC / R;
-    extern __shared__ float2 sm[];
-    float2* lines = sm;
-    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
-    const int W = a.W;
-    const int c = blockIdx.x * LPC + lc;
-    const size_t P = size_t(NC) * W;
-    float acc[R];
-#pragma unroll
-    for (int e = 0; e < R; ++e) acc[e] = 0.f;
-    for (int j = blockIdx.y; j < a.pairs; j += a.groups) {
-        const float2* z = a.zbuf + size_t(j) * P;
-        float2 v[R];
-#pragma unroll
-        for (int e = 0; e < R; ++e) v[e] = z[size_t(t + T * e) * W + c];
-        line_fft<NC, R, -1, true>(v, lines + lc * col_stride<NC>(), t, a.tw);
-#pragma unroll
-        for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
-    }
-    float* S = a.sacc + size_t(blockIdx.y) * P;
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-        const size_t i = size_t(t + T * e) * W + c;
-        S[i] = a.accumulate ? S[i] + acc[e] : acc[e];
-    }
-}
 
 // ---------------------------------------------------------------- finalize ----
 // I(k) = I(-k) = (sum_g S_g(k) + S_g(-k)) * scale: one thread per pixel pair {k, -k}
@@ -302,105 +52,95 @@ __global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, 
 }
 
 // ------------------------------------------------------------------- host ----
-template <int NC>
-static int launch_col_ifft(const OsprArgs& a, cudaStream_t st) {
-    static uint64_t mask = 0;
-    constexpr size_t smem = col_ifft_smem_bytes<NC>();
-    int rc = ensure_smem((const void*)k_ospr_col_ifft<NC>, smem, &mask);
-    if (rc) return rc;
-    dim3 grid(a.W / ColCfg<NC>::LPC, a.pairs);
-    Launch ln("ospr_col_ifft", st);
-    k_ospr_col_ifft<NC><<<grid, (NC / ColCfg<NC>::R) * ColCfg<NC>::LPC, smem, st>>>(a);
-    return ln.done("ospr_col_ifft launch");
-}
-
-template <int NR, bool REPLAY>
-static int launch_row(const OsprArgs& a, cudaStream_t st) {
-    static uint64_t mask = 0;
-    constexpr size_t smem = row_smem_bytes<NR>();
-    int rc = ensure_smem((const void*)k_ospr_row<NR, REPLAY>, smem, &mask);
-    if (rc) return rc;
-    dim3 grid(a.H / RowCfg<NR>::LPR, a.pairs);
-    Launch ln("ospr_row", st);
-    k_ospr_row<NR, REPLAY><<<grid, (NR / RowCfg<NR>::R) * RowCfg<NR>::LPR, smem, st>>>(a);
-    return ln.done("ospr_row launch");
-}
-
-template <int NC>
-static int launch_col_fft(const OsprArgs& a, cudaStream_t st) {
-    static uint64_t mask = 0;
-    constexpr size_t smem = col_fft_smem_bytes<NC>();
-    int rc = ensure_smem((const void*)k_ospr_col_fft<NC>, smem, &mask);
-    if (rc) return rc;
-    dim3 grid(a.W / ColCfg<NC>::LPC, a.groups);
-    Launch ln("ospr_col_fft", st);
-    k_ospr_col_fft<NC><<<grid, (NC / ColCfg<NC>::R) * ColCfg<NC>::LPC, smem, st>>>(a);
-    return ln.done("ospr_col_fft launch");
-}
-
-#define HOLO_LEN_SWITCH(n, CALL)                          \
-    switch (n) {                                          \
-        case 64: return CALL(64);                         \
-        case 128: return CALL(128);                       \
-        case 256: return CALL(256);                       \
-        case 512: return CALL(512);                       \
-        case 1024: return CALL(1024);                     \
-        case 2048: return CALL(2048);                     \
-        case 4096: return CALL(4096);                     \
-        default: return fail(HOLO_EUNSUPPORTED, "line length %d", n); \
-    }
-
-static int run_col_ifft(const OsprArgs& a, cudaStream_t st) {
-#define C(n) launch_col_ifft<n>(a, st)
-    HOLO_LEN_SWITCH(a.H, C)
-#undef C
-}
-static int run_row(const OsprArgs& a, bool replay, cudaStream_t st) {
-#define C(n) (replay ? launch_row<n, true>(a, st) : launch_row<n, false>(a, st))
-    HOLO_LEN_SWITCH(a.W, C)
-#undef C
-}
-static int run_col_fft(const OsprArgs& a, cudaStream_t st) {
-#define C(n) launch_col_fft<n>(a, st)
-    HOLO_LEN_SWITCH(a.H, C)
-#undef C
-}
-
-struct OsprPlan {
-    int npairs, chunk, groups;
-    size_t z_bytes, s_bytes, total;
+// Per-shape tuning: tile variants of the column and row passes, pairs in flight (chunk)
+// and partial accumulators (groups). Defaults: variant 0, 16 pairs, 4 groups (overridable
+// with HOLO_OSPR_CHUNK / HOLO_OSPR_GROUPS); ospr_autotune replaces them per shape with
+// the fastest measured candidate, and HOLO_TUNE_CACHE names a file that keeps the choices
+// across processes. The workspace size follows the tuning of the shape.
+struct OsprTuning {
+    int col_v, row_v, chunk, groups;
 };
 
-// Tuning override: HOLO_OSPR_CHUNK (pairs in flight, 1..16) and HOLO_OSPR_GROUPS
-// (partial accumulators, 1..4) replace the defaults; read once per process.
 static int env_int(const char* name, int lo, int hi, int dflt) {
     const char* v = getenv(name);
     if (!v || !*v) return dflt;
     const int x = atoi(v);
     return x < lo ? lo : (x > hi ? hi : x);
 }
-static int tuned_chunk() {
-    static const int v = env_int("HOLO_OSPR_CHUNK", 1, kMaxChunkPairs, kMaxChunkPairs);
-    return v;
-}
-static int tuned_groups() {
-    static const int v = env_int("HOLO_OSPR_GROUPS", 1, kMaxGroups, kMaxGroups);
-    return v;
+
+static OsprTuning default_tuning() {
+    static const OsprTuning t{0, 0, env_int("HOLO_OSPR_CHUNK", 1, kMaxChunkPairs, kMaxChunkPairs),
+                              env_int("HOLO_OSPR_GROUPS", 1, kMaxGroups, kMaxGroups)};
+    return t;
 }
 
-static OsprPlan ospr_plan(int H, int W, int N) {
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, OsprTuning> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_cache_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("HOLO_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    int H, W, cv, rv, ch, gr;
+    while (fscanf(f, " {\"H\": %d, \"W\": %d, \"col_variant\": %d, \"row_variant\": %d, \"chunk\": %d, "
+                     "\"groups\": %d}", &H, &W, &cv, &rv, &ch, &gr) == 6) {
+        if (cv < 0 || cv > 1 || rv < 0 || rv > 1 || ch < 1 || ch > kMaxChunkPairs || gr < 1 || gr > kMaxGroups)
+            continue;
+        g_tune[{H, W}] = OsprTuning{has_variant(H) ? cv : 0, has_variant(W) ? rv : 0, ch, gr};
+    }
+    fclose(f);
+}
+
+static void tune_cache_save_locked() {
+    const char* path = getenv("HOLO_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (const auto& kv : g_tune)
+        fprintf(f, "{\"H\": %d, \"W\": %d, \"col_variant\": %d, \"row_variant\": %d, \"chunk\": %d, "
+                   "\"groups\": %d}\n", kv.first.first, kv.first.second, kv.second.col_v, kv.second.row_v,
+                kv.second.chunk, kv.second.groups);
+    fclose(f);
+}
+
+static OsprTuning tuning_for(int H, int W) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load_locked();
+    auto it = g_tune.find({H, W});
+    return it == g_tune.end() ? default_tuning() : it->second;
+}
+
+static void tuning_install(int H, int W, const OsprTuning& t, bool save) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load_locked();
+    g_tune[{H, W}] = t;
+    if (save) tune_cache_save_locked();
+}
+
+struct OsprPlan {
+    int npairs, chunk, groups, col_v, row_v;
+    size_t z_bytes, s_bytes, total;
+};
+
+static OsprPlan ospr_plan_with(int H, int W, int N, const OsprTuning& t) {
     OsprPlan pl;
     const size_t P = size_t(H) * W;
     pl.npairs = (N + 1) / 2;
-    const int cmax = tuned_chunk();
-    pl.chunk = pl.npairs < cmax ? pl.npairs : cmax;
-    const int gmax = tuned_groups();
-    pl.groups = pl.chunk < gmax ? pl.chunk : gmax;
+    pl.chunk = pl.npairs < t.chunk ? pl.npairs : t.chunk;
+    pl.groups = pl.chunk < t.groups ? pl.chunk : t.groups;
+    pl.col_v = has_variant(H) ? t.col_v : 0;
+    pl.row_v = has_variant(W) ? t.row_v : 0;
     pl.z_bytes = align_up(size_t(pl.chunk) * P * sizeof(float2), 256);
     pl.s_bytes = align_up(size_t(pl.groups) * P * sizeof(float), 256);
     pl.total = pl.z_bytes + pl.s_bytes;
     return pl;
 }
+
+static OsprPlan ospr_plan(int H, int W, int N) { return ospr_plan_with(H, W, N, tuning_for(H, W)); }
 
 static bool is_prime(int64_t n) {
     if (n < 2) return false;
@@ -413,6 +153,29 @@ static int check_shape(const char* who, int H, int W) {
     if (!is_pow2(H) || !is_pow2(W) || H < kMinDim || W < kMinDim || H > kMaxDim || W > kMaxDim)
         return fail(HOLO_EUNSUPPORTED, "%s: H=%d W=%d must be powers of two in [%d, %d]", who, H, W,
                     kMinDim, kMaxDim);
+    return HOLO_OK;
+}
+
+// chunks of sub-frame pairs through the three passes, then the symmetrising finalize
+static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_replay, cudaStream_t st) {
+    int rc;
+    for (int first = 0; first < pl.npairs; first += pl.chunk) {
+        a.first_pair = first;
+        a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
+        a.accumulate = first > 0;
+        if ((rc = ospr_run_col_ifft(a, pl.col_v, st))) return rc;
+        if ((rc = ospr_run_row(a, pl.row_v, replay, st))) return rc;
+        if (replay && (rc = ospr_run_col_fft(a, pl.col_v, st))) return rc;
+    }
+    if (replay) {
+        const size_t P = size_t(a.H) * a.W;
+        const float scale = float(1.0 / (2.0 * double(a.N) * double(P)));
+        const int threads = 256;
+        const int blocks = int((P / 2 + a.W + threads - 1) / threads);
+        Launch ln("ospr_finalize", st);
+        k_ospr_finalize<<<blocks, threads, 0, st>>>(a.sacc, pl.groups, a.H, a.W, scale, d_replay);
+        if ((rc = ln.done("ospr_finalize launch"))) return rc;
+    }
     return HOLO_OK;
 }
 
@@ -472,30 +235,126 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.bits = d_holo_bits;
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-    const bool replay = d_replay != nullptr;
-    for (int first = 0; first < pl.npairs; first += pl.chunk) {
-        a.first_pair = first;
-        a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
-        a.accumulate = first > 0;
-        if ((rc = run_col_ifft(a, st))) return rc;
-        if ((rc = run_row(a, replay, st))) return rc;
-        if (replay && (rc = run_col_fft(a, st))) return rc;
-    }
-    if (replay) {
-        const float scale = float(1.0 / (2.0 * double(N) * double(P)));
-        const int threads = 256;
-        const int blocks = int((P / 2 + W + threads - 1) / threads);
-        Launch ln("ospr_finalize", st);
-        k_ospr_finalize<<<blocks, threads, 0, st>>>(a.sacc, pl.groups, H, W, scale, d_replay);
-        if ((rc = ln.done("ospr_finalize launch"))) return rc;
-    }
+    if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
     // Section 8 design rules: warnings only
     if (L > 0) {
         if (!is_prime(L)) warn("design rule: L=%lld is not prime", (long long)L);
         if (L <= N) warn("design rule: L=%lld is not greater than N=%d", (long long)L, N);
         if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
     }
+    return HOLO_OK;
+}
+
+extern "C" int ospr_tuning_get(int H, int W, int* col_variant, int* row_variant, int* chunk, int* groups) {
+    clear_error();
+    int rc = check_shape("ospr_tuning_get", H, W);
+    if (rc) return rc;
+    if (!col_variant || !row_variant || !chunk || !groups) return fail(HOLO_EINVAL, "ospr_tuning_get: NULL output");
+    const OsprTuning t = tuning_for(H, W);
+    *col_variant = has_variant(H) ? t.col_v : 0;
+    *row_variant = has_variant(W) ? t.row_v : 0;
+    *chunk = t.chunk;
+    *groups = t.groups;
+    return HOLO_OK;
+}
+
+extern "C" int ospr_tuning_set(int H, int W, int col_variant, int row_variant, int chunk, int groups) {
+    clear_error();
+    int rc = check_shape("ospr_tuning_set", H, W);
+    if (rc) return rc;
+    if (col_variant < 0 || col_variant > 1 || row_variant < 0 || row_variant > 1 || chunk < 1 ||
+        chunk > kMaxChunkPairs || groups < 1 || groups > kMaxGroups)
+        return fail(HOLO_EINVAL, "ospr_tuning_set: variants 0..1, chunk 1..%d, groups 1..%d", kMaxChunkPairs,
+                    kMaxGroups);
+    tuning_install(H, W, OsprTuning{has_variant(H) ? col_variant : 0, has_variant(W) ? row_variant : 0, chunk,
+                                    groups}, false);
+    return HOLO_OK;
+}
+
+extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, double* best_ms) {
+    clear_error();
+    const char* who = "ospr_autotune";
+    int rc = check_shape(who, H, W);
+    if (rc) return rc;
+    if (N < 1 || N > 4096 || reps < 1 || reps > 100) return fail(HOLO_EINVAL, "%s: N=%d reps=%d", who, N, reps);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    const size_t P = size_t(H) * W;
+    const int64_t L = 10007;
+    // the largest candidate plan bounds the workspace
+    const size_t ws_bytes = ospr_plan_with(H, W, N, OsprTuning{0, 0, kMaxChunkPairs, kMaxGroups}).total;
+    void *d_t = nullptr, *d_codes = nullptr, *d_bits = nullptr, *d_rep = nullptr, *d_ws = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaMalloc(&d_t, P * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_codes, size_t(L));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_bits, size_t(N) * P / 8);
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_rep, P * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMalloc(&d_ws, ws_bytes);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        cudaFree(d_t); cudaFree(d_codes); cudaFree(d_bits); cudaFree(d_rep); cudaFree(d_ws);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (ce != cudaSuccess) {
+        release();
+        return fail(HOLO_ENOMEM, "%s: scratch allocation failed: %s", who, cudaGetErrorString(ce));
+    }
+    rc = cuda_status(cudaMemsetAsync(d_t, 0x3c, P * sizeof(float), st), "ospr_autotune: fill");
+    if (!rc) rc = lut_build(7, L, 256, static_cast<uint8_t*>(d_codes), nullptr, s);
+    const OsprTuning before = tuning_for(H, W);
+    const int npairs = (N + 1) / 2;
+    // time one candidate: one warm-up call, then the median of `reps` calls
+    auto measure = [&](const OsprTuning& t, float* ms) -> int {
+        tuning_install(H, W, t, false);
+        int r = ospr_generate(static_cast<const float*>(d_t), H, W, N, static_cast<const uint8_t*>(d_codes), L, 256, 7,
+                              0, 0, HOLO_FP32, static_cast<uint32_t*>(d_bits), static_cast<float*>(d_rep), d_ws,
+                              ws_bytes, s);
+        if (r) return r;
+        float v[100];
+        for (int i = 0; i < reps; ++i) {
+            cudaEventRecord(e0, st);
+            r = ospr_generate(static_cast<const float*>(d_t), H, W, N, static_cast<const uint8_t*>(d_codes), L, 256,
+                              7, 0, 0, HOLO_FP32, static_cast<uint32_t*>(d_bits), static_cast<float*>(d_rep), d_ws,
+                              ws_bytes, s);
+            if (r) return r;
+            cudaEventRecord(e1, st);
+            cudaError_t x = cudaEventSynchronize(e1);
+            if (x != cudaSuccess) return cuda_status(x, "ospr_autotune: timing");
+            cudaEventElapsedTime(&v[i], e0, e1);
+        }
+        std::sort(v, v + reps);
+        *ms = v[reps / 2];
+        return HOLO_OK;
+    };
+    OsprTuning best{0, 0, kMaxChunkPairs < npairs ? kMaxChunkPairs : npairs, kMaxGroups};
+    float best_t = 0.f;
+    if (!rc) rc = measure(best, &best_t);
+    // coordinate descent over tile variants, pairs in flight, accumulator groups
+    auto consider = [&](OsprTuning t) {
+        if (rc) return;
+        float ms = 0.f;
+        rc = measure(t, &ms);
+        if (!rc && ms < best_t) { best_t = ms; best = t; }
+    };
+    if (has_variant(H)) { OsprTuning t = best; t.col_v = 1; consider(t); }
+    if (has_variant(W)) { OsprTuning t = best; t.row_v = 1; consider(t); }
+    const int chunks[] = {2, 4, 8, 12, 16};
+    const OsprTuning base = best;
+    for (int c : chunks)
+        if (c < npairs && c != base.chunk) { OsprTuning t = base; t.chunk = c; consider(t); }
+    const OsprTuning base2 = best;
+    const int groups[] = {1, 2, 4};
+    for (int g : groups)
+        if (g != base2.groups && g <= base2.chunk) { OsprTuning t = base2; t.groups = g; consider(t); }
+    release();
+    if (rc) {
+        tuning_install(H, W, before, false);
+        return rc;
+    }
+    tuning_install(H, W, best, true);
+    if (best_ms) *best_ms = best_t;
     return HOLO_OK;
 }
 
@@ -542,6 +401,8 @@ static bool noalloc_plan(int H, int W, int N, OsprPlan* pl) {
     pl->chunk = chunk;
     pl->z_bytes = align_up(size_t(chunk) * P * sizeof(float2), 256);
     pl->total = pl->z_bytes + pl->s_bytes;
+    pl->col_v = 0;
+    pl->row_v = 0;
     return pl->total <= size_t(HOLO_NOALLOC_SCRATCH_BYTES);
 }
 
@@ -589,25 +450,7 @@ extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
     a.bits = d_holo_bits;
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-    const bool replay = d_replay != nullptr;
     // every scratch byte a kernel reads was written earlier in this call (the first chunk
     // overwrites the accumulator), so nothing needs clearing between calls
-    for (int first = 0; first < pl.npairs; first += pl.chunk) {
-        a.first_pair = first;
-        a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
-        a.accumulate = first > 0;
-        if ((rc = run_col_ifft(a, st))) return rc;
-        if ((rc = run_row(a, replay, st))) return rc;
-        if (replay && (rc = run_col_fft(a, st))) return rc;
-    }
-    if (replay) {
-        const float scale = float(1.0 / (2.0 * double(N) * double(P)));
-        const int threads = 256;
-        const int blocks = int((P / 2 + W + threads - 1) / threads);
-        Launch ln("ospr_finalize", st);
-        k_ospr_finalize<<<blocks, threads, 0, st>>>(a.sacc, pl.groups, H, W, scale, d_replay);
-        if ((rc = ln.done("ospr_finalize launch"))) return rc;
-    }
-    return HOLO_OK;
+    return ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s));
 }

@@ -1,0 +1,46 @@
+// ospr_col.cu - launchers of the OSPR column passes (build + column IDFT; column DFT +
+// accumulate) for every supported column length and tile variant.
+#include "ospr_kernels.cuh"
+
+namespace holo {
+
+template <int NC, int V>
+static int launch_col_ifft(const OsprArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = col_ifft_smem_bytes<NC, V>();
+    int rc = ensure_smem((const void*)k_ospr_col_ifft<NC, V>, smem, &mask);
+    if (rc) return rc;
+    dim3 grid(a.W / ColCfg<NC, V>::LPC, a.pairs);
+    Launch ln("ospr_col_ifft", st);
+    k_ospr_col_ifft<NC, V><<<grid, (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC, smem, st>>>(a);
+    return ln.done("ospr_col_ifft launch");
+}
+
+template <int NC, int V>
+static int launch_col_fft(const OsprArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = col_fft_smem_bytes<NC, V>();
+    int rc = ensure_smem((const void*)k_ospr_col_fft<NC, V>, smem, &mask);
+    if (rc) return rc;
+    dim3 grid(a.W / ColCfg<NC, V>::LPC, a.groups);
+    Launch ln("ospr_col_fft", st);
+    k_ospr_col_fft<NC, V><<<grid, (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC, smem, st>>>(a);
+    return ln.done("ospr_col_fft launch");
+}
+
+#define HOLO_COL_SWITCH(n, v, F)                                              \
+    switch (n) {                                                              \
+        case 64: return F<64, 0>(a, st);                                      \
+        case 128: return F<128, 0>(a, st);                                    \
+        case 256: return F<256, 0>(a, st);                                    \
+        case 512: return v ? F<512, 1>(a, st) : F<512, 0>(a, st);             \
+        case 1024: return v ? F<1024, 1>(a, st) : F<1024, 0>(a, st);          \
+        case 2048: return v ? F<2048, 1>(a, st) : F<2048, 0>(a, st);          \
+        case 4096: return v ? F<4096, 1>(a, st) : F<4096, 0>(a, st);          \
+        default: return fail(HOLO_EUNSUPPORTED, "column length %d", n);      \
+    }
+
+int ospr_run_col_ifft(const OsprArgs& a, int v, cudaStream_t st) { HOLO_COL_SWITCH(a.H, v, launch_col_ifft) }
+int ospr_run_col_fft(const OsprArgs& a, int v, cudaStream_t st) { HOLO_COL_SWITCH(a.H, v, launch_col_fft) }
+
+}  // namespace holo

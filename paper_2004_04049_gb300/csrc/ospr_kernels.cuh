@@ -1,0 +1,299 @@
+// ospr_kernels.cuh - kernels of binary-phase One-Step Phase-Retrieval (paper Sections 2, 3, 5.2, 6).
+//
+// Per sub-frame s: E = T*exp(i*theta_s) with theta_s from the LUT draw rule (Fig. 3),
+// H_s = IDFT(E) (Eq. 2), h_s = sign(Re H_s) with sign(0) = +1, and the replay
+// I = (1/N) sum_s |DFT(h_s)|^2 (Eq. 1).
+//
+// Only Re H_s is needed and h_s is real, so sub-frames go through the transforms in
+// pairs (s0, s1) = (2j, 2j+1):
+//   * IDFT of the Hermitian part E^h(k) = E(k) + conj(E(-k)) is real and equals
+//     2 Re IDFT(E), so one complex IDFT of Z = E^h_{s0} + i E^h_{s1} gives
+//     Re H_{s0} (real part) and Re H_{s1} (imaginary part) at once, up to a positive
+//     factor the binarisation ignores;
+//   * DFT(h_{s0} + i h_{s1}) = R_{s0} + i R_{s1} with R real-input spectra, and
+//     |R_{s0}(k)|^2 + |R_{s1}(k)|^2 = (|Z(k)|^2 + |Z(-k)|^2)/2, so the kernels
+//     accumulate S = sum |Z|^2 and the last step symmetrises S(k) + S(-k).
+// An odd N leaves one sub-frame that is transformed alone (Z = E, h imaginary part 0).
+//
+// Three passes per chunk of pairs, each one global round trip of a complex field:
+//   col_ifft  columns: build Z from the target and the table, column IDFT
+//   row       rows:    row IDFT, binarise (bits out), row DFT of h_{s0} + i h_{s1}
+//   col_fft   columns: column DFT, S += |Z|^2 over the pairs of a group
+// then finalize: I(k) = (sum_g S_g(k) + S_g(-k)) / (2*N*H*W).
+#pragma once
+
+#include "fft_core.cuh"
+#include "phase_source.cuh"
+#include "runtime.h"
+
+namespace holo {
+
+// Launch shapes per line length and tile variant V (the autotuner picks V per shape).
+// Column passes hold LPC columns of T = N/R threads with R elements each; row passes use
+// T >= 32 threads per row so that a warp holds 32 consecutive pixels.
+template <int N, int V> struct ColCfg;
+template <> struct ColCfg<64, 0>   { static constexpr int R = 8,  LPC = 32; };
+template <> struct ColCfg<128, 0>  { static constexpr int R = 16, LPC = 32; };
+template <> struct ColCfg<256, 0>  { static constexpr int R = 16, LPC = 32; };
+template <> struct ColCfg<512, 0>  { static constexpr int R = 16, LPC = 16; };
+template <> struct ColCfg<1024, 0> { static constexpr int R = 32, LPC = 16; };
+template <> struct ColCfg<2048, 0> { static constexpr int R = 32, LPC = 8; };
+template <> struct ColCfg<4096, 0> { static constexpr int R = 32, LPC = 4; };
+template <> struct ColCfg<512, 1>  { static constexpr int R = 32, LPC = 16; };
+template <> struct ColCfg<1024, 1> { static constexpr int R = 32, LPC = 8; };
+template <> struct ColCfg<2048, 1> { static constexpr int R = 32, LPC = 4; };
+template <> struct ColCfg<4096, 1> { static constexpr int R = 32, LPC = 2; };
+template <int N, int V> struct RowCfg;
+template <> struct RowCfg<64, 0>   { static constexpr int R = 2,  LPR = 4; };
+template <> struct RowCfg<128, 0>  { static constexpr int R = 4,  LPR = 4; };
+template <> struct RowCfg<256, 0>  { static constexpr int R = 8,  LPR = 4; };
+template <> struct RowCfg<512, 0>  { static constexpr int R = 16, LPR = 4; };
+template <> struct RowCfg<1024, 0> { static constexpr int R = 32, LPR = 4; };
+template <> struct RowCfg<2048, 0> { static constexpr int R = 32, LPR = 2; };
+template <> struct RowCfg<4096, 0> { static constexpr int R = 32, LPR = 1; };
+template <> struct RowCfg<512, 1>  { static constexpr int R = 8,  LPR = 4; };
+template <> struct RowCfg<1024, 1> { static constexpr int R = 16, LPR = 2; };
+template <> struct RowCfg<2048, 1> { static constexpr int R = 16, LPR = 1; };
+template <> struct RowCfg<4096, 1> { static constexpr int R = 16, LPR = 1; };
+// lengths with a second tile variant
+constexpr bool has_variant(int N) { return N >= 512; }
+
+constexpr int kMaxChunkPairs = 16;   // pairs whose fields are in flight at once
+constexpr int kMaxGroups = 4;        // partial accumulators of the column DFT pass
+
+struct OsprArgs {
+    const float* target;
+    int H, W, N;
+    PhaseSource ps;
+    float2* zbuf;         // [chunk pairs][H][W]
+    float* sacc;          // [groups][H][W]
+    int groups;
+    int first_pair;       // global index of the chunk's pair 0
+    int pairs;            // pairs in this chunk
+    uint32_t* bits;       // [N][H*W/32] or null
+    int accumulate;       // add to sacc instead of overwriting
+    const float2* tw;
+    const float2* cs256;
+};
+
+template <int NC, int V>
+constexpr int col_stride() { return col_line_stride(NC, ColCfg<NC, V>::R, ColCfg<NC, V>::LPC); }
+// pass 1 also holds the replicated cos/sin table
+template <int NC, int V>
+constexpr size_t col_ifft_smem_bytes() {
+    return sizeof(float2) * (kCsSmemEntries + size_t(ColCfg<NC, V>::LPC) * col_stride<NC, V>());
+}
+template <int NC, int V>
+constexpr size_t col_fft_smem_bytes() {
+    return sizeof(float2) * size_t(ColCfg<NC, V>::LPC) * col_stride<NC, V>();
+}
+template <int NR, int V>
+constexpr size_t row_smem_bytes() {
+    return sizeof(float2) * size_t(RowCfg<NR, V>::LPR) * line_stride(NR, RowCfg<NR, V>::R);
+}
+
+// ------------------------------------------------------------------ pass 1 ----
+// Z for one column of one pair, in canonical layout (slot e <-> row t + T*e). MODE and
+// SINGLE are compile-time so that the element loops hold no branches: for each batch of
+// kBatch elements every load (target, mirror target, four codes) is issued before any
+// of them is used.
+constexpr int kBatch = 8;
+
+template <int NC, int V, int MODE, bool SINGLE>
+__device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R], const OsprArgs& a,
+                                                  const float2* cs, int t, int c, int s0) {
+    constexpr int R = ColCfg<NC, V>::R, T = NC / R;
+    constexpr int B = R < kBatch ? R : kBatch;
+    const int W = a.W;
+    const int cm = (W - c) & (W - 1);
+    const int sh = a.ps.cs_shift;
+    const SubframeDraw d0 = subframe_draw(a.ps, s0);
+    const SubframeDraw d1 = subframe_draw(a.ps, SINGLE ? s0 : s0 + 1);
+    // table mode: indices (start + s*stride + p) mod L advance by D = T*W mod L per element;
+    // the mirror pixel of row r = t + T*e is (H - r)*W + cm = q0 - e*T*W, except for row 0
+    const uint32_t L = a.ps.L;
+    const uint64_t fm = a.ps.fm;
+    uint32_t D = 0, i0 = 0, i1 = 0, m0 = 0, m1 = 0, z0 = 0, z1 = 0;
+    if constexpr (MODE == kPhaseTable) {
+        D = uint32_t((uint64_t(T) * uint64_t(W)) % L);
+        const uint32_t p0 = uint32_t(t) * uint32_t(W) + uint32_t(c);
+        const uint32_t q0 = uint32_t(NC - t) * uint32_t(W) + uint32_t(cm);
+        i0 = fastmod_u32(d0.base_mod + p0, fm, L);
+        i1 = fastmod_u32(d1.base_mod + p0, fm, L);
+        m0 = fastmod_u32(d0.base_mod + q0, fm, L);
+        m1 = fastmod_u32(d1.base_mod + q0, fm, L);
+        z0 = fastmod_u32(d0.base_mod + uint32_t(cm), fm, L);
+        z1 = fastmod_u32(d1.base_mod + uint32_t(cm), fm, L);
+    }
+    const int gshift = 64 - a.ps.bits;
+#pragma unroll
+    for (int e0 = 0; e0 < R; e0 += B) {
+        float tp[B], tm[B];
+        uint32_t pk[B];   // codes of (s0, p), (s0, -p), (s1, p), (s1, -p), one byte each
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int e = e0 + k;
+            const int r = t + T * e;
+            const int rm = (NC - r) & (NC - 1);
+            tp[k] = __ldg(a.target + r * W + c);
+            tm[k] = SINGLE ? 0.f : __ldg(a.target + rm * W + cm);
+            if constexpr (MODE == kPhaseTable) {
+                const uint32_t jm0 = (e == 0 && t == 0) ? z0 : m0;
+                const uint32_t jm1 = (e == 0 && t == 0) ? z1 : m1;
+                uint32_t w = __ldg(a.ps.codes + i0);
+                if constexpr (!SINGLE) {
+                    w |= uint32_t(__ldg(a.ps.codes + jm0)) << 8;
+                    w |= uint32_t(__ldg(a.ps.codes + i1)) << 16;
+                    w |= uint32_t(__ldg(a.ps.codes + jm1)) << 24;
+                }
+                pk[k] = w;
+                i0 += D; i0 -= (i0 >= L) ? L : 0u;
+                i1 += D; i1 -= (i1 >= L) ? L : 0u;
+                m0 = (m0 >= D) ? m0 - D : m0 + (L - D);
+                m1 = (m1 >= D) ? m1 - D : m1 + (L - D);
+            } else if constexpr (MODE == kPhaseGenerator) {
+                const uint64_t p = uint64_t(r) * uint64_t(W) + uint64_t(c);
+                const uint64_t pm = uint64_t(rm) * uint64_t(W) + uint64_t(cm);
+                uint32_t w = uint32_t(splitmix64_at(a.ps.seed, d0.base + p) >> gshift);
+                if constexpr (!SINGLE) {
+                    w |= uint32_t(splitmix64_at(a.ps.seed, d0.base + pm) >> gshift) << 8;
+                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + p) >> gshift) << 16;
+                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + pm) >> gshift) << 24;
+                }
+                pk[k] = w;
+            } else {
+                pk[k] = 0u;   // flat phase
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const float2 c0 = cs_lookup(cs, (pk[k] & 0xffu) << sh);
+            if constexpr (SINGLE) {
+                v[e0 + k] = make_float2(tp[k] * c0.x, tp[k] * c0.y);
+            } else {
+                const float2 c0m = cs_lookup(cs, ((pk[k] >> 8) & 0xffu) << sh);
+                const float2 c1 = cs_lookup(cs, ((pk[k] >> 16) & 0xffu) << sh);
+                const float2 c1m = cs_lookup(cs, (pk[k] >> 24) << sh);
+                // Hermitian parts E(k) + conj(E(-k)) of both sub-frames, packed as a + i b
+                const float2 h0 = make_float2(fmaf(tp[k], c0.x, tm[k] * c0m.x), fmaf(tp[k], c0.y, -tm[k] * c0m.y));
+                const float2 h1 = make_float2(fmaf(tp[k], c1.x, tm[k] * c1m.x), fmaf(tp[k], c1.y, -tm[k] * c1m.y));
+                v[e0 + k] = make_float2(h0.x - h1.y, h0.y + h1.x);
+            }
+        }
+    }
+}
+
+template <int NC, int V>
+__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
+k_ospr_col_ifft(OsprArgs a) {
+    constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R;
+    extern __shared__ float2 sm[];
+    float2* cs = sm;
+    float2* lines = sm + kCsSmemEntries;
+    load_cs_table(cs, a.cs256);
+    __syncthreads();
+
+    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
+    const int W = a.W;
+    const int c = blockIdx.x * LPC + lc;
+    const int s0 = 2 * (a.first_pair + int(blockIdx.y));
+    const bool single = s0 + 1 >= a.N;
+    float2 v[R];
+    if (a.ps.mode == kPhaseTable) {
+        if (single) ospr_build_column<NC, V, kPhaseTable, true>(v, a, cs, t, c, s0);
+        else ospr_build_column<NC, V, kPhaseTable, false>(v, a, cs, t, c, s0);
+    } else if (a.ps.mode == kPhaseGenerator) {
+        if (single) ospr_build_column<NC, V, kPhaseGenerator, true>(v, a, cs, t, c, s0);
+        else ospr_build_column<NC, V, kPhaseGenerator, false>(v, a, cs, t, c, s0);
+    } else {
+        if (single) ospr_build_column<NC, V, kPhaseFlat, true>(v, a, cs, t, c, s0);
+        else ospr_build_column<NC, V, kPhaseFlat, false>(v, a, cs, t, c, s0);
+    }
+    line_fft<NC, R, +1, true>(v, lines + lc * col_stride<NC, V>(), t, a.tw);
+    float2* z = a.zbuf + size_t(blockIdx.y) * size_t(NC) * size_t(W);
+#pragma unroll
+    for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
+}
+
+// ------------------------------------------------------------------ pass 2 ----
+template <int NR, int V, bool REPLAY>
+__global__ void __launch_bounds__((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR)
+k_ospr_row(OsprArgs a) {
+    constexpr int R = RowCfg<NR, V>::R, T = NR / R;
+    constexpr bool BLOCK = T > 32;
+    extern __shared__ float2 sm[];
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * RowCfg<NR, V>::LPR + line;
+    const int s0 = 2 * (a.first_pair + int(blockIdx.y));
+    const bool single = s0 + 1 >= a.N;
+    const size_t P = size_t(a.H) * NR;
+    float2* z = a.zbuf + size_t(blockIdx.y) * P + size_t(r) * NR;
+    float2* buf = sm + line * line_stride(NR, R);
+
+    float2 v[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
+    line_fft<NR, R, +1, BLOCK>(v, buf, t, a.tw);
+
+    const size_t words = P / 32;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const bool n0 = v[e].x < 0.f;
+        const bool n1 = v[e].y < 0.f;
+        if (a.bits) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, n0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, n1);
+            if (lane == 0) {
+                const size_t w = (size_t(r) * NR + size_t(t - lane + T * e)) >> 5;
+                a.bits[size_t(s0) * words + w] = b0;
+                if (!single) a.bits[size_t(s0 + 1) * words + w] = b1;
+            }
+        }
+        v[e] = make_float2(n0 ? -1.f : 1.f, single ? 0.f : (n1 ? -1.f : 1.f));
+    }
+    if constexpr (REPLAY) {
+        line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
+#pragma unroll
+        for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
+    }
+}
+
+// ------------------------------------------------------------------ pass 3 ----
+template <int NC, int V>
+__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
+k_ospr_col_fft(OsprArgs a) {
+    constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R;
+    extern __shared__ float2 sm[];
+    float2* lines = sm;
+    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
+    const int W = a.W;
+    const int c = blockIdx.x * LPC + lc;
+    const size_t P = size_t(NC) * W;
+    float acc[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) acc[e] = 0.f;
+    for (int j = blockIdx.y; j < a.pairs; j += a.groups) {
+        const float2* z = a.zbuf + size_t(j) * P;
+        float2 v[R];
+#pragma unroll
+        for (int e = 0; e < R; ++e) v[e] = z[size_t(t + T * e) * W + c];
+        line_fft<NC, R, -1, true>(v, lines + lc * col_stride<NC, V>(), t, a.tw);
+#pragma unroll
+        for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
+    }
+    float* S = a.sacc + size_t(blockIdx.y) * P;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const size_t i = size_t(t + T * e) * W + c;
+        S[i] = a.accumulate ? S[i] + acc[e] : acc[e];
+    }
+}
+
+
+// pass launchers (ospr_col.cu, ospr_row.cu); `v` selects the tile variant
+int ospr_run_col_ifft(const OsprArgs& a, int v, cudaStream_t st);
+int ospr_run_col_fft(const OsprArgs& a, int v, cudaStream_t st);
+int ospr_run_row(const OsprArgs& a, int v, bool replay, cudaStream_t st);
+
+}  // namespace holo

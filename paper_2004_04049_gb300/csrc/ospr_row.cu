@@ -1,0 +1,37 @@
+// ospr_row.cu - launchers of the OSPR row pass (row IDFT, binarise, row DFT) for every
+// supported row length and tile variant.
+#include "ospr_kernels.cuh"
+
+namespace holo {
+
+template <int NR, int V, bool REPLAY>
+static int launch_row(const OsprArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = row_smem_bytes<NR, V>();
+    int rc = ensure_smem((const void*)k_ospr_row<NR, V, REPLAY>, smem, &mask);
+    if (rc) return rc;
+    dim3 grid(a.H / RowCfg<NR, V>::LPR, a.pairs);
+    Launch ln("ospr_row", st);
+    k_ospr_row<NR, V, REPLAY><<<grid, (NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR, smem, st>>>(a);
+    return ln.done("ospr_row launch");
+}
+
+template <int NR, int V>
+static int launch_row_any(const OsprArgs& a, bool replay, cudaStream_t st) {
+    return replay ? launch_row<NR, V, true>(a, st) : launch_row<NR, V, false>(a, st);
+}
+
+int ospr_run_row(const OsprArgs& a, int v, bool replay, cudaStream_t st) {
+    switch (a.W) {
+        case 64: return launch_row_any<64, 0>(a, replay, st);
+        case 128: return launch_row_any<128, 0>(a, replay, st);
+        case 256: return launch_row_any<256, 0>(a, replay, st);
+        case 512: return v ? launch_row_any<512, 1>(a, replay, st) : launch_row_any<512, 0>(a, replay, st);
+        case 1024: return v ? launch_row_any<1024, 1>(a, replay, st) : launch_row_any<1024, 0>(a, replay, st);
+        case 2048: return v ? launch_row_any<2048, 1>(a, replay, st) : launch_row_any<2048, 0>(a, replay, st);
+        case 4096: return v ? launch_row_any<4096, 1>(a, replay, st) : launch_row_any<4096, 0>(a, replay, st);
+        default: return fail(HOLO_EUNSUPPORTED, "row length %d", a.W);
+    }
+}
+
+}  // namespace holo

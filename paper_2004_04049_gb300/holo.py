@@ -82,6 +82,9 @@ _SIGS = {
                                            _c.POINTER(_c.c_void_p)]),
     "holo_graph_launch": (_c.c_int, [_c.c_void_p, _c.c_void_p]),
     "holo_graph_destroy": (_c.c_int, [_c.c_void_p]),
+    "ospr_autotune": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.POINTER(_c.c_double)]),
+    "ospr_tuning_get": (_c.c_int, [_c.c_int, _c.c_int] + [_c.POINTER(_c.c_int)] * 4),
+    "ospr_tuning_set": (_c.c_int, [_c.c_int] * 6),
     "gs_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "gs_iterate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
                               _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
@@ -248,6 +251,27 @@ def holo_graph_launch(graph, stream=None):
 
 def holo_graph_destroy(graph):
     return _call("holo_graph_destroy", graph)
+
+
+def ospr_autotune(H, W, N, reps=3, stream=None):
+    """Times candidate tunings for this shape and installs the fastest; returns ms per call."""
+    ms = ctypes.c_double(0.0)
+    s = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else None)
+    if s is None:
+        import torch
+        s = torch.cuda.current_stream().cuda_stream
+    _call("ospr_autotune", H, W, N, reps, s, ctypes.byref(ms))
+    return ms.value
+
+
+def ospr_tuning_get(H, W):
+    v = [ctypes.c_int(0) for _ in range(4)]
+    _call("ospr_tuning_get", H, W, *[ctypes.byref(x) for x in v])
+    return {"col_variant": v[0].value, "row_variant": v[1].value, "chunk": v[2].value, "groups": v[3].value}
+
+
+def ospr_tuning_set(H, W, col_variant=0, row_variant=0, chunk=16, groups=4):
+    return _call("ospr_tuning_set", H, W, col_variant, row_variant, chunk, groups)
 
 
 def gs_workspace_size(H, W, iters, precision=HOLO_FP32):
