@@ -310,6 +310,7 @@ def run_ours(args):
     nmse = errs[:, 2].cpu().numpy()
 
     batch = run_batch_leg(dev, stream) if not args.no_batch else None
+    precision_leg = run_precision_leg(dev, stream) if not args.no_batch else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -340,6 +341,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": len(L_SWEEP) * 4 * P,
                     "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 4 * P + 24)},
             "batch": batch,
+            "precision": precision_leg,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -427,6 +429,58 @@ def run_batch_leg(dev, stream, reps=3):
             "per_frame_launches": sub / (t_pf / 1e3), "batch_call": sub / (t_batch / 1e3),
             "graph_launch": sub / (t_graph / 1e3), "ms": {"per_frame": t_pf, "batch": t_batch, "graph": t_graph},
             "tuning": tunings}
+
+
+# --------------------------------------------------------- mixed precision leg ----
+def run_precision_leg(dev, stream, reps=5):
+    """OSPR at 1024^2 and 2048^2, N = 24, L = 10007, in float32 and with the DFT-32 stages
+    on the tensor cores (fp16 / bf16 hi+lo operands, float32 accumulation). Errors are
+    against the float32 path of the same run (the tests bound them against the oracle)."""
+    import torch
+
+    from paper_2004_04049_gb300 import holo, pipeline
+    from synthetic import blob_target
+
+    out = {}
+    s = stream.cuda_stream
+    for n in (1024, 2048):
+        T = torch.from_numpy(blob_target(n, n, 1000)).to(dev)
+        codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
+        res = {}
+        ref = None
+        for name, prec in (("fp32", holo.HOLO_FP32), ("fp16x2", holo.HOLO_FP16X2), ("bf16x2", holo.HOLO_BF16X2)):
+            ws = torch.empty(holo.ospr_workspace_size(n, n, N_SF, prec), dtype=torch.uint8, device=dev)
+            bits = torch.empty((N_SF, n * n // 32), dtype=torch.int32, device=dev)
+            I = torch.empty((n, n), dtype=torch.float32, device=dev)
+
+            def call():
+                pipeline.ospr(T, N_SF, codes, GS_L, 256, LUT_SEED, ws=ws, out_bits=bits, out_replay=I,
+                              precision=prec, stream=s)
+
+            call()
+            torch.cuda.synchronize(dev)
+            ms = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            err = pipeline.error(I, T, stream=s).cpu().numpy()
+            r = {"subframes_per_s": N_SF / (float(np.median(ms)) / 1e3), "nmse": float(err[2])}
+            if ref is None:
+                ref = (bits.clone(), I.clone(), float(err[2]))
+            else:
+                b0 = np.unpackbits(ref[0].cpu().numpy().view(np.uint8))
+                b1 = np.unpackbits(bits.cpu().numpy().view(np.uint8))
+                r["bits_agree_vs_fp32"] = float(np.mean(b0 == b1))
+                r["replay_rel_vs_fp32"] = float((I - ref[1]).abs().max().item() / ref[1].abs().max().item())
+                r["nmse_rel_vs_fp32"] = abs(float(err[2]) - ref[2]) / ref[2]
+            res[name] = r
+        out[f"{n}x{n}"] = res
+    return out
 
 
 # ------------------------------------------------------------- CPU oracle arm ----

@@ -123,6 +123,7 @@ static void tuning_install(int H, int W, const OsprTuning& t, bool save) {
 
 struct OsprPlan {
     int npairs, chunk, groups, col_v, row_v;
+    int prec = HOLO_FP32;
     size_t z_bytes, s_bytes, total;
 };
 
@@ -140,7 +141,28 @@ static OsprPlan ospr_plan_with(int H, int W, int N, const OsprTuning& t) {
     return pl;
 }
 
-static OsprPlan ospr_plan(int H, int W, int N) { return ospr_plan_with(H, W, N, tuning_for(H, W)); }
+static bool tc_shape(int H, int W) { return (H == 1024 || H == 2048) && (W == 1024 || W == 2048); }
+
+// tensor-core precisions use fixed tile variants (radix-32 lines in two buffers)
+static OsprPlan ospr_plan(int H, int W, int N, int precision = HOLO_FP32) {
+    OsprTuning t = tuning_for(H, W);
+    if (precision != HOLO_FP32) {
+        t.col_v = kTcColVariant;
+        t.row_v = kTcRowVariant;
+    }
+    OsprPlan pl = ospr_plan_with(H, W, N, t);
+    pl.prec = precision;
+    return pl;
+}
+
+static int check_precision(const char* who, int precision, int H, int W) {
+    if (precision == HOLO_FP32) return HOLO_OK;
+    if (precision != HOLO_FP16X2 && precision != HOLO_BF16X2)
+        return fail(HOLO_EINVAL, "%s: unknown precision %d", who, precision);
+    if (!tc_shape(H, W))
+        return fail(HOLO_EUNSUPPORTED, "%s: tensor-core precisions need H, W in {1024, 2048} (got %dx%d)", who, H, W);
+    return HOLO_OK;
+}
 
 static bool is_prime(int64_t n) {
     if (n < 2) return false;
@@ -163,9 +185,15 @@ static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_repla
         a.first_pair = first;
         a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
         a.accumulate = first > 0;
-        if ((rc = ospr_run_col_ifft(a, pl.col_v, st))) return rc;
-        if ((rc = ospr_run_row(a, pl.row_v, replay, st))) return rc;
-        if (replay && (rc = ospr_run_col_fft(a, pl.col_v, st))) return rc;
+        if (pl.prec == HOLO_FP32) {
+            if ((rc = ospr_run_col_ifft(a, pl.col_v, st))) return rc;
+            if ((rc = ospr_run_row(a, pl.row_v, replay, st))) return rc;
+            if (replay && (rc = ospr_run_col_fft(a, pl.col_v, st))) return rc;
+        } else {
+            if ((rc = ospr_run_col_ifft_tc(a, pl.prec, st))) return rc;
+            if ((rc = ospr_run_row_tc(a, pl.prec, replay, st))) return rc;
+            if (replay && (rc = ospr_run_col_fft_tc(a, pl.prec, st))) return rc;
+        }
     }
     if (replay) {
         const size_t P = size_t(a.H) * a.W;
@@ -189,8 +217,8 @@ extern "C" int ospr_workspace_size(int H, int W, int N, int precision, size_t* b
     int rc = check_shape("ospr_workspace_size", H, W);
     if (rc) return rc;
     if (N < 1 || N > 4096) return fail(HOLO_EINVAL, "ospr_workspace_size: N=%d out of [1, 4096]", N);
-    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "ospr_workspace_size: precision %d", precision);
-    *bytes = ospr_plan(H, W, N).total;
+    if ((rc = check_precision("ospr_workspace_size", precision, H, W))) return rc;
+    *bytes = ospr_plan(H, W, N, precision).total;
     return HOLO_OK;
 }
 
@@ -204,7 +232,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     int rc = check_shape(who, H, W);
     if (rc) return rc;
     if (N < 1 || N > 4096) return fail(HOLO_EINVAL, "%s: N=%d out of [1, 4096]", who, N);
-    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "%s: precision %d is not built", who, precision);
+    if ((rc = check_precision(who, precision, H, W))) return rc;
     if (!d_target) return fail(HOLO_EINVAL, "%s: d_target is NULL", who);
     if (!d_holo_bits && !d_replay) return fail(HOLO_EINVAL, "%s: both outputs are NULL", who);
     const int64_t P = int64_t(H) * W;
@@ -214,7 +242,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     PhaseSource ps;
     rc = make_phase_source(who, d_codes, L, levels, seed, start_index, stride, &ps);
     if (rc) return rc;
-    const OsprPlan pl = ospr_plan(H, W, N);
+    const OsprPlan pl = ospr_plan(H, W, N, precision);
     if (!d_ws || ws_bytes < pl.total)
         return fail(HOLO_EWORKSPACE, "%s: workspace %zu bytes, need %zu", who, ws_bytes, pl.total);
     if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0)
@@ -235,6 +263,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.bits = d_holo_bits;
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
+    a.tc = tab.tc[precision];
     if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
     // Section 8 design rules: warnings only
     if (L > 0) {
@@ -444,6 +473,7 @@ extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
     a.W = W;
     a.N = N;
     a.ps = ps;
+    a.tc = nullptr;
     a.zbuf = static_cast<float2*>(scratch);
     a.sacc = reinterpret_cast<float*>(static_cast<char*>(scratch) + pl.z_bytes);
     a.groups = pl.groups;

@@ -25,6 +25,7 @@
 #include "fft_core.cuh"
 #include "phase_source.cuh"
 #include "runtime.h"
+#include "tc_dft.cuh"
 
 namespace holo {
 
@@ -74,22 +75,60 @@ struct OsprArgs {
     int accumulate;       // add to sacc instead of overwriting
     const float2* tw;
     const float2* cs256;
+    const TcFrags* tc;    // DFT-32 A fragments of the tensor-core precision in use
 };
 
 template <int NC, int V>
 constexpr int col_stride() { return col_line_stride(NC, ColCfg<NC, V>::R, ColCfg<NC, V>::LPC); }
+// tensor-core precisions stage every line in two buffers (PREC != 0)
+constexpr int nbuf(int prec) { return prec ? 2 : 1; }
 // pass 1 also holds the replicated cos/sin table
-template <int NC, int V>
+template <int NC, int V, int PREC = 0>
 constexpr size_t col_ifft_smem_bytes() {
-    return sizeof(float2) * (kCsSmemEntries + size_t(ColCfg<NC, V>::LPC) * col_stride<NC, V>());
+    return sizeof(float2) * (kCsSmemEntries + size_t(nbuf(PREC)) * ColCfg<NC, V>::LPC * col_stride<NC, V>());
 }
-template <int NC, int V>
+template <int NC, int V, int PREC = 0>
 constexpr size_t col_fft_smem_bytes() {
-    return sizeof(float2) * size_t(ColCfg<NC, V>::LPC) * col_stride<NC, V>();
+    return sizeof(float2) * size_t(nbuf(PREC)) * ColCfg<NC, V>::LPC * col_stride<NC, V>();
 }
-template <int NR, int V>
+template <int NR, int V, int PREC = 0>
 constexpr size_t row_smem_bytes() {
-    return sizeof(float2) * size_t(RowCfg<NR, V>::LPR) * line_stride(NR, RowCfg<NR, V>::R);
+    return sizeof(float2) * size_t(nbuf(PREC)) * RowCfg<NR, V>::LPR * line_stride(NR, RowCfg<NR, V>::R);
+}
+
+// Line FFT of a column pass: `lines` holds LPC line buffers (and LPC more for the
+// tensor-core precisions, whose warps each work on one line: warp w on line w / WPL).
+template <int NC, int V, int DIR, int PREC>
+__device__ __forceinline__ void col_line_fft(float2 (&v)[ColCfg<NC, V>::R], float2* lines, int lc, int t,
+                                             const OsprArgs& a) {
+    constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, S = col_stride<NC, V>();
+    if constexpr (PREC == 0) {
+        line_fft<NC, R, DIR, true>(v, lines + lc * S, t, a.tw);
+    } else {
+        static_assert(R == 32 && (NC == 1024 || NC == 2048), "tensor-core stages need radix-32 lines");
+        constexpr int WPL = (NC / R) / 32;
+        float2* lines2 = lines + LPC * S;
+        const int warp = threadIdx.x >> 5;
+        const int wline = warp / WPL, wl = warp % WPL;
+        line_fft_tc<NC, DIR, PREC>(v, lines + lc * S, lines2 + lc * S, lines + wline * S, lines2 + wline * S, t, wl,
+                                   a.tc, a.tw);
+    }
+}
+
+// Line FFT of a row pass: line `line` of LPR, T = N/R threads per line.
+template <int NR, int V, int DIR, int PREC>
+__device__ __forceinline__ void row_line_fft(float2 (&v)[RowCfg<NR, V>::R], float2* lines, int line, int t,
+                                             const OsprArgs& a) {
+    constexpr int R = RowCfg<NR, V>::R, LPR = RowCfg<NR, V>::LPR, T = NR / R;
+    constexpr int S = line_stride(NR, R);
+    if constexpr (PREC == 0) {
+        line_fft<NR, R, DIR, (T > 32)>(v, lines + line * S, t, a.tw);
+    } else {
+        static_assert(R == 32 && (NR == 1024 || NR == 2048), "tensor-core stages need radix-32 lines");
+        float2* lines2 = lines + LPR * S;
+        line_fft_tc<NR, DIR, PREC>(v, lines + line * S, lines2 + line * S, lines + line * S, lines2 + line * S, t,
+                                   t >> 5, a.tc, a.tw);
+    }
 }
 
 // ------------------------------------------------------------------ pass 1 ----
@@ -183,7 +222,7 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
     }
 }
 
-template <int NC, int V>
+template <int NC, int V, int PREC>
 __global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
 k_ospr_col_ifft(OsprArgs a) {
     constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R;
@@ -209,14 +248,14 @@ k_ospr_col_ifft(OsprArgs a) {
         if (single) ospr_build_column<NC, V, kPhaseFlat, true>(v, a, cs, t, c, s0);
         else ospr_build_column<NC, V, kPhaseFlat, false>(v, a, cs, t, c, s0);
     }
-    line_fft<NC, R, +1, true>(v, lines + lc * col_stride<NC, V>(), t, a.tw);
+    col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
     float2* z = a.zbuf + size_t(blockIdx.y) * size_t(NC) * size_t(W);
 #pragma unroll
     for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
 }
 
 // ------------------------------------------------------------------ pass 2 ----
-template <int NR, int V, bool REPLAY>
+template <int NR, int V, bool REPLAY, int PREC>
 __global__ void __launch_bounds__((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR)
 k_ospr_row(OsprArgs a) {
     constexpr int R = RowCfg<NR, V>::R, T = NR / R;
@@ -229,12 +268,10 @@ k_ospr_row(OsprArgs a) {
     const bool single = s0 + 1 >= a.N;
     const size_t P = size_t(a.H) * NR;
     float2* z = a.zbuf + size_t(blockIdx.y) * P + size_t(r) * NR;
-    float2* buf = sm + line * line_stride(NR, R);
-
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
-    line_fft<NR, R, +1, BLOCK>(v, buf, t, a.tw);
+    row_line_fft<NR, V, +1, PREC>(v, sm, line, t, a);
 
     const size_t words = P / 32;
 #pragma unroll
@@ -253,14 +290,14 @@ k_ospr_row(OsprArgs a) {
         v[e] = make_float2(n0 ? -1.f : 1.f, single ? 0.f : (n1 ? -1.f : 1.f));
     }
     if constexpr (REPLAY) {
-        line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
+        row_line_fft<NR, V, -1, PREC>(v, sm, line, t, a);
 #pragma unroll
         for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
     }
 }
 
 // ------------------------------------------------------------------ pass 3 ----
-template <int NC, int V>
+template <int NC, int V, int PREC>
 __global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
 k_ospr_col_fft(OsprArgs a) {
     constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R;
@@ -278,7 +315,7 @@ k_ospr_col_fft(OsprArgs a) {
         float2 v[R];
 #pragma unroll
         for (int e = 0; e < R; ++e) v[e] = z[size_t(t + T * e) * W + c];
-        line_fft<NC, R, -1, true>(v, lines + lc * col_stride<NC, V>(), t, a.tw);
+        col_line_fft<NC, V, -1, PREC>(v, lines, lc, t, a);
 #pragma unroll
         for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
     }
@@ -295,5 +332,11 @@ k_ospr_col_fft(OsprArgs a) {
 int ospr_run_col_ifft(const OsprArgs& a, int v, cudaStream_t st);
 int ospr_run_col_fft(const OsprArgs& a, int v, cudaStream_t st);
 int ospr_run_row(const OsprArgs& a, int v, bool replay, cudaStream_t st);
+// tensor-core precisions (ospr_tc.cu): lengths 1024 and 2048, fixed tile variants
+int ospr_run_col_ifft_tc(const OsprArgs& a, int prec, cudaStream_t st);
+int ospr_run_col_fft_tc(const OsprArgs& a, int prec, cudaStream_t st);
+int ospr_run_row_tc(const OsprArgs& a, int prec, bool replay, cudaStream_t st);
+constexpr int kTcColVariant = 1;
+constexpr int kTcRowVariant = 0;
 
 }  // namespace holo

@@ -8,11 +8,11 @@ template <int NR, int V, bool REPLAY>
 static int launch_row(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
     constexpr size_t smem = row_smem_bytes<NR, V>();
-    int rc = ensure_smem((const void*)k_ospr_row<NR, V, REPLAY>, smem, &mask);
+    int rc = ensure_smem((const void*)k_ospr_row<NR, V, REPLAY, 0>, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.H / RowCfg<NR, V>::LPR, a.pairs);
     Launch ln("ospr_row", st);
-    k_ospr_row<NR, V, REPLAY><<<grid, (NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR, smem, st>>>(a);
+    k_ospr_row<NR, V, REPLAY, 0><<<grid, (NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR, smem, st>>>(a);
     return ln.done("ospr_row launch");
 }
 

@@ -38,9 +38,11 @@ class Launch {
 int profiling_swap(int on);
 
 // ---- constant tables ---------------------------------------------------------
+struct TcFrags;
 struct Tables {
     const float2* twiddles;   // Stockham stage twiddles, see fft_core.cuh
     const float2* cs256;      // (cos, sin)(2*pi*c/256), c < 256
+    const TcFrags* tc[3];     // DFT-32 A fragments per tensor-core precision (index 1 fp16, 2 bf16)
 };
 // Fills the tables on the current device the first time and returns their addresses.
 int device_tables(Tables* out);

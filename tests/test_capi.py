@@ -64,7 +64,12 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert rc == holo.HOLO_EINVAL
     rc = lib.ospr_generate(1 << 20, 256, 256, 4, None, 0, 256, 0, 0, 0, 7, None, 1 << 20, 1 << 20,
                            1 << 30, None)
+    assert rc == holo.HOLO_EINVAL
+    # tensor-core precisions exist for line lengths 1024 and 2048 only
+    rc = lib.ospr_generate(1 << 20, 256, 256, 4, None, 0, 256, 0, 0, 0, holo.HOLO_BF16X2, None, 1 << 20,
+                           1 << 20, 1 << 30, None)
     assert rc == holo.HOLO_EUNSUPPORTED
+    assert holo.ospr_workspace_size(1024, 2048, 24, holo.HOLO_FP16X2) > 0
     rc = lib.ospr_generate(1 << 20, 256, 256, 4, None, 0, 256, 0, 0, 0, 0, None, 1 << 20, 1 << 20,
                            16, None)
     assert rc == holo.HOLO_EWORKSPACE
