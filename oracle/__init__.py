@@ -20,4 +20,4 @@ Readings of points the paper leaves open are listed in the design notes and repe
 each function's docstring.
 """
 
-from . import fft, lut, ospr, gs, error  # noqa: F401
+from . import conv, fft, lut, ospr, gs, error  # noqa: F401
