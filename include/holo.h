@@ -77,7 +77,8 @@ int holo_launch_count(uint64_t* out_count);
  * milliseconds since the last holo_profile_reset. Families: "lut_build",
  * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "gs_prepare",
  * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2",
- * "err_finish". */
+ * "err_finish", "nn_conv_fwd", "nn_conv_dgrad", "nn_conv_wgrad", "nn_elementwise",
+ * "nn_loss", "nn_adam". */
 int holo_profile_enable(int on);
 int holo_profile_reset(void);
 int holo_profile_read(const char* name, uint64_t* launches, double* total_ms);
@@ -298,6 +299,73 @@ int gs_iterate(const float* d_target, int H, int W, int iters, int levels,
                uint8_t* d_phase_codes, float* d_replay, double* d_err,
                const float* d_state_in, float* d_state_out,
                void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/* ------------------------------------------------------- learned warm start ---- */
+
+/*
+ * A learned GS starting phase. Not in the paper: an engineering extension whose fallback
+ * and judge is the paper's random start (Section 3). A 4-level convolutional
+ * encoder-decoder (3x3 convolutions, 32/64/128/128 channels, 2x2 average pooling, nearest
+ * 2x upsampling with additive skips, ReLU) maps a target amplitude, area-averaged to
+ * 256x256, to two channels (u, v) whose angle is the predicted replay-plane phase. It is
+ * trained on (target, phase) pairs produced by gs_iterate with the offset-invariant loss
+ * L = mean_b [1 - |sum_p w_p y_p conj(z_p)| / sum_p w_p], y = (u+iv)/|u+iv|, z = exp(i
+ * label), w = target^2 (a global phase offset, which GS leaves free, costs nothing).
+ * Weights are float32 masters with Adam (beta 0.9/0.999, eps 1e-8); every convolution
+ * runs as a bf16 implicit GEMM on the tensor cores with float32 accumulation.
+ *
+ * The network owns its device memory (parameters, optimizer state and activations for
+ * up to max_batch samples; HOLO_ENOMEM if allocation fails) on the device current at
+ * creation; calls must run with that device current.
+ *   ws_net_create      seeded He-normal initialisation (SplitMix64 + Box-Muller).
+ *   ws_train_step      one Adam step on a batch: d_targets [batch][256][256] float32
+ *                      amplitudes, d_label_phase [batch][256][256] radians; d_loss
+ *                      (nullable) receives the batch loss (float32, device).
+ *   ws_forward_backward  the same without the update (gradients readable by ws_get_tensor).
+ *   ws_infer           one target d_target [H][W] (square, H a multiple of 256) ->
+ *                      d_phase_out [H][W] radians: the 256x256 prediction resampled
+ *                      bilinearly on (u, v); feed it to gs_iterate's d_init_phase.
+ *   ws_get_tensor / ws_set_tensor  host copies of layer `layer` (0..11): which = 0 weights
+ *                      [Cout][3][3][Cin], 1 biases, 2 weight gradients, 3 bias gradients
+ *                      (set: 0 and 1 only); count must equal the tensor size.
+ *   ws_layer_shape     input channels, output channels and resolution of a layer.
+ *   ws_get_activation  host float32 copy of a stored tensor of the last forward/backward
+ *                      for `batch` samples: "x0" (input), "a1" "s1" "p1" "a2" "s2" "p2" "a3"
+ *                      "s3" "p3" "a4" "b4" "up4" "u5" "up5" "u6" "up6" "u7" (activations),
+ *                      "out" (float32 head output, 8 channels), "g_out" "g_u7" "g_up6"
+ *                      "g_u6" "g_s1" (gradients); count must equal the tensor size.
+ *   ws_save / ws_load  weights and Adam state to / from a binary file.
+ */
+typedef struct ws_net ws_net;
+int ws_net_create(ws_net** out, uint64_t seed, int max_batch);
+int ws_net_destroy(ws_net* net);
+int ws_net_param_count(const ws_net* net, int64_t* count);
+int ws_train_step(ws_net* net, const float* d_targets, const float* d_label_phase, int batch, float lr,
+                  float* d_loss, holo_stream_t s);
+int ws_forward_backward(ws_net* net, const float* d_targets, const float* d_label_phase, int batch,
+                        float* d_loss, holo_stream_t s);
+int ws_infer(ws_net* net, const float* d_target, int H, int W, float* d_phase_out, holo_stream_t s);
+int ws_get_tensor(const ws_net* net, int layer, int which, float* h_out, int64_t count);
+int ws_set_tensor(ws_net* net, int layer, int which, const float* h_in, int64_t count);
+int ws_layer_shape(int layer, int* cin, int* cout, int* resolution);
+int ws_get_activation(const ws_net* net, const char* name, int batch, float* h_out, int64_t count);
+int ws_save(const ws_net* net, const char* path);
+int ws_load(ws_net* net, const char* path);
+
+/*
+ * nn_conv3x3 - the network's convolution kernel on its own (3x3, zero padding 1, stride
+ * 1, channels-last bf16 tensors, channels multiples of 8, float32 accumulation):
+ *   mode 0 forward: d_out[p][o] = act(sum X(p,k) W[o][k] + bias[o] + residual[p][o]) with
+ *          d_in [B][H][W][Cin], d_wmat [Cout][9*Cin] bf16, bias/residual nullable,
+ *          outputs bf16 d_out and/or float32 d_out_f32;
+ *   mode 1 input gradient: as mode 0 with d_in = dy [B][H][W][Cin] and d_wmat the
+ *          transposed weights [Cout][9*Cin] = W^T of the layer, offsets flipped;
+ *   mode 2 weight gradient: d_dw [Cout][9*Cin] float32 += sum_p d_dy[p][o] X(p, k) with
+ *          d_in = x [B][H][W][Cin], d_dy [B][H][W][Cout].
+ */
+int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, const void* d_in, const void* d_wmat,
+               const void* d_dy, const float* d_bias, const void* d_residual, int relu, void* d_out,
+               float* d_out_f32, float* d_dw, holo_stream_t s);
 
 /* ------------------------------------------------------------ replay error ---- */
 

@@ -23,7 +23,7 @@ def conv3x3(x, w, b=None):
     y = np.zeros((B, H, W, Co))
     for ky in range(3):
         for kx in range(3):
-            y += np.einsum("bhwi,oi->bhwo", xp[:, ky:ky + H, kx:kx + W, :], w[:, ky, kx, :])
+            y += np.einsum("bhwi,oi->bhwo", xp[:, ky:ky + H, kx:kx + W, :], w[:, ky, kx, :], optimize=True)
     if b is not None:
         y += np.asarray(b, np.float64)
     return y
@@ -41,7 +41,7 @@ def conv3x3_dgrad(dy, w):
     for ky in range(3):
         for kx in range(3):
             # x position p receives dy at p - (ky - 1): in padded coordinates p + 1 - (ky - 1)
-            dx += np.einsum("bhwo,oi->bhwi", dyp[:, 2 - ky:2 - ky + H, 2 - kx:2 - kx + W, :], w[:, ky, kx, :])
+            dx += np.einsum("bhwo,oi->bhwi", dyp[:, 2 - ky:2 - ky + H, 2 - kx:2 - kx + W, :], w[:, ky, kx, :], optimize=True)
     return dx
 
 
@@ -56,7 +56,7 @@ def conv3x3_wgrad(x, dy):
     dw = np.zeros((Co, 3, 3, Ci))
     for ky in range(3):
         for kx in range(3):
-            dw[:, ky, kx, :] = np.einsum("bhwo,bhwi->oi", dy, xp[:, ky:ky + H, kx:kx + W, :])
+            dw[:, ky, kx, :] = np.einsum("bhwo,bhwi->oi", dy, xp[:, ky:ky + H, kx:kx + W, :], optimize=True)
     return dw
 
 

@@ -90,6 +90,22 @@ _SIGS = {
                               _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
                               _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                               _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "ws_net_create": (_c.c_int, [_c.POINTER(_c.c_void_p), _c.c_uint64, _c.c_int]),
+    "ws_net_destroy": (_c.c_int, [_c.c_void_p]),
+    "ws_net_param_count": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_int64)]),
+    "ws_train_step": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_float, _c.c_void_p,
+                                 _c.c_void_p]),
+    "ws_forward_backward": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p]),
+    "ws_infer": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_void_p]),
+    "ws_get_tensor": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_int64]),
+    "ws_set_tensor": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_int64]),
+    "ws_layer_shape": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "ws_get_activation": (_c.c_int, [_c.c_void_p, _c.c_char_p, _c.c_int, _c.c_void_p, _c.c_int64]),
+    "ws_save": (_c.c_int, [_c.c_void_p, _c.c_char_p]),
+    "ws_load": (_c.c_int, [_c.c_void_p, _c.c_char_p]),
+    "nn_conv3x3": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.c_void_p,
+                              _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p,
+                              _c.c_void_p, _c.c_void_p]),
     "replay_error_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "replay_error": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int,
                                 _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
@@ -302,3 +318,87 @@ def replay_error(d_replay, d_target, d_mask, H, W, d_out, d_ws, ws_bytes=None, s
         ws_bytes = d_ws.numel() * d_ws.element_size()
     return _call("replay_error", _ptr(d_replay), _ptr(d_target), _ptr(d_mask), H, W, _ptr(d_out),
                  _ptr(d_ws), ws_bytes, _stream(stream, d_replay))
+
+
+# -------------------------------------------------------- learned warm start ----
+def ws_net_create(seed, max_batch):
+    h = ctypes.c_void_p(0)
+    _call("ws_net_create", ctypes.byref(h), seed, max_batch)
+    return h.value
+
+
+def ws_net_destroy(net):
+    return _call("ws_net_destroy", net)
+
+
+def ws_net_param_count(net):
+    n = ctypes.c_int64(0)
+    _call("ws_net_param_count", net, ctypes.byref(n))
+    return n.value
+
+
+def ws_train_step(net, d_targets, d_label_phase, batch, lr, d_loss=None, stream=None):
+    return _call("ws_train_step", net, _ptr(d_targets), _ptr(d_label_phase), batch, lr, _ptr(d_loss),
+                 _stream(stream, d_targets))
+
+
+def ws_forward_backward(net, d_targets, d_label_phase, batch, d_loss=None, stream=None):
+    return _call("ws_forward_backward", net, _ptr(d_targets), _ptr(d_label_phase), batch, _ptr(d_loss),
+                 _stream(stream, d_targets))
+
+
+def ws_infer(net, d_target, H, W, d_phase_out, stream=None):
+    return _call("ws_infer", net, _ptr(d_target), H, W, _ptr(d_phase_out), _stream(stream, d_target))
+
+
+def ws_layer_shape(layer):
+    a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _call("ws_layer_shape", layer, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
+
+
+def ws_get_tensor(net, layer, which):
+    """Host numpy copy: which 0 weights [Cout,3,3,Cin], 1 biases, 2 dW, 3 db."""
+    import numpy as np
+    cin, cout, _ = ws_layer_shape(layer)
+    shape = (cout, 3, 3, cin) if which in (0, 2) else (cout,)
+    out = np.zeros(shape, dtype=np.float32)
+    _call("ws_get_tensor", net, layer, which, out.ctypes.data, out.size)
+    return out
+
+
+def ws_set_tensor(net, layer, which, array):
+    import numpy as np
+    a = np.ascontiguousarray(array, dtype=np.float32)
+    return _call("ws_set_tensor", net, layer, which, a.ctypes.data, a.size)
+
+
+_ACT_SHAPES = {"x0": (8, 1), "a1": (32, 1), "s1": (32, 1), "p1": (32, 2), "a2": (64, 2), "s2": (64, 2),
+               "p2": (64, 4), "a3": (128, 4), "s3": (128, 4), "p3": (128, 8), "a4": (128, 8), "b4": (128, 8),
+               "up4": (128, 4), "u5": (128, 4), "up5": (128, 2), "u6": (64, 2), "up6": (64, 1), "u7": (32, 1),
+               "out": (8, 1), "g_out": (8, 1), "g_u7": (32, 1), "g_up6": (64, 1), "g_u6": (64, 2), "g_s1": (32, 1)}
+
+
+def ws_get_activation(net, name, batch=1):
+    """Host float32 copy [batch, H, W, C] of a stored tensor of the last pass."""
+    import numpy as np
+    c, div = _ACT_SHAPES[name]
+    r = 256 // div
+    out = np.zeros((batch, r, r, c), dtype=np.float32)
+    _call("ws_get_activation", net, name.encode(), batch, out.ctypes.data, out.size)
+    return out
+
+
+def ws_save(net, path):
+    return _call("ws_save", net, str(path).encode())
+
+
+def ws_load(net, path):
+    return _call("ws_load", net, str(path).encode())
+
+
+def nn_conv3x3(mode, B, H, W, Cin, Cout, d_in, d_wmat=None, d_dy=None, d_bias=None, d_residual=None, relu=False,
+               d_out=None, d_out_f32=None, d_dw=None, stream=None):
+    return _call("nn_conv3x3", mode, B, H, W, Cin, Cout, _ptr(d_in), _ptr(d_wmat), _ptr(d_dy), _ptr(d_bias),
+                 _ptr(d_residual), 1 if relu else 0, _ptr(d_out), _ptr(d_out_f32), _ptr(d_dw),
+                 _stream(stream, d_in))
