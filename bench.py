@@ -545,6 +545,55 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Learned GS warm start at the configured scale (labels from 100-iteration GS on 20k
+    seeded 256^2 targets, training by the library's kernels, evaluation at 1024^2), plus
+    the tensor-core throughput of the network's convolution kernel."""
+    import torch
+
+    from paper_2004_04049_gb300 import build_lib, holo, warmstart
+
+    build_lib.build()
+    holo.load()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    conv = {}
+    for name, (B, R, C) in {"c1b_32ch_256sq": (16, 256, 32), "c3b_128ch_64sq": (16, 64, 128)}.items():
+        x = torch.randn((B, R, R, C), device=dev).to(torch.bfloat16)
+        w = (0.05 * torch.randn((C, 9 * C), device=dev)).to(torch.bfloat16)
+        y = torch.empty((B, R, R, C), dtype=torch.bfloat16, device=dev)
+        flops = 2.0 * B * R * R * C * C * 9
+
+        def call():
+            holo.nn_conv3x3(0, B, R, R, C, C, x, w, d_out=y, relu=True, stream=stream.cuda_stream)
+
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            call()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        conv[name] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
+    res = warmstart.run(n_train=args.learned_n, gs_iters=100, epochs=args.learned_epochs, batch=16,
+                        eval_size=1024, n_eval=8, log=lambda s: print(s, file=sys.stderr))
+    peaks = _peaks()
+    ev = res["eval"]
+    line = {"metric": "learned GS warm start: GS iterations to the 20-iteration LUT-random error at 1024^2",
+            "n_train": args.learned_n, "epochs": args.learned_epochs,
+            "loss_first": float(np.mean(res["losses"][:20])), "loss_last": float(np.mean(res["losses"][-20:])),
+            "iters_lut_mean": float(np.mean([r["iters_lut"] for r in ev])),
+            "iters_learned_mean": float(np.mean([r["iters_learned"] or 60 for r in ev])),
+            "ms_lut_mean": float(np.mean([r["ms_lut"] for r in ev])),
+            "ms_learned_mean": float(np.mean([r["ms_learned"] or np.nan for r in ev])),
+            "eval": ev, "seconds": res["seconds"], "conv_kernel": conv,
+            "bf16_peak_tflops": peaks["bf16_tflops"] if peaks else 1900.0}
+    print(json.dumps(line), flush=True)
+
+
 def run_case(name):
     """Small fixed workloads for profiler captures (no timing, no JSON line)."""
     import torch
@@ -578,7 +627,13 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default FFT tiles and chunking")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--case", default=None, help="run a small fixed workload for a profiler capture")
+    ap.add_argument("--learned", action="store_true", help="run the learned GS warm-start experiment")
+    ap.add_argument("--learned-n", type=int, default=20000)
+    ap.add_argument("--learned-epochs", type=int, default=2)
     args = ap.parse_args()
+    if args.learned:
+        run_learned(args)
+        return
     if args.case:
         from paper_2004_04049_gb300 import build_lib
         build_lib.build()
