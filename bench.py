@@ -16,6 +16,8 @@ the host cores instead (a bounded sample of the same workload).
 """
 
 import argparse
+import csv
+import hashlib
 import json
 import os
 import subprocess
@@ -145,6 +147,86 @@ def subframe_bytes(P, N, L):
     return 16 * P + P // 8 + (4 * P + 8 * P + lut) / N
 
 
+# ------------------------------------------------------------ DRAM traffic ----
+# `traffic` in the roofline object is dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch of the dominant kernel, from an ncu capture recorded in profiles/dram_traffic.json
+# by `bench.py --record-traffic <ncu csv>`. Each record carries a digest of the sources the
+# kernel is compiled from; once they change the record no longer applies and traffic is null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+CSRC = os.path.join(ROOT, "paper_2004_04049_gb300", "csrc")
+KERNEL_SOURCES = {
+    "ospr_col_ifft": ["ospr_kernels.cuh", "fft_core.cuh", "phase_source.cuh", "ospr_col.cu", "tc_dft.cuh"],
+    "ospr_col_fft": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_col.cu", "tc_dft.cuh"],
+    "ospr_row": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_row.cu", "tc_dft.cuh"],
+    "ospr_finalize": ["ospr.cu"],
+}
+KERNEL_FAMILY = {"k_ospr_col_ifft": "ospr_col_ifft", "k_ospr_col_fft": "ospr_col_fft", "k_ospr_row": "ospr_row",
+                 "k_ospr_finalize": "ospr_finalize"}
+
+
+def sources_digest(family):
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[family]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def record_traffic(csv_path, command, out_path=TRAFFIC_FILE):
+    """Per-launch DRAM bytes of the OSPR kernels from an ncu --csv metrics log."""
+    with open(csv_path) as fh:
+        rows = [r for r in csv.reader(fh)]
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hdr]
+    ki, mi, vi, gi = h.index("Kernel Name"), h.index("Metric Name"), h.index("Metric Value"), h.index("Grid Size")
+    out = {}
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi:
+            continue
+        name = r[ki].replace("void ", "").split("(")[0]
+        fam = KERNEL_FAMILY.get(name.split("<")[0])
+        if fam is None:
+            continue
+        rec = out.setdefault(fam, {"kernel": name, "grid": r[gi], "sources": sources_digest(fam),
+                                   "command": command})
+        if rec["kernel"] != name or rec["grid"] != r[gi]:
+            continue   # first launch of the family only
+        rec[r[mi]] = float(r[vi].replace(",", ""))
+    old = {}
+    if os.path.exists(out_path):
+        with open(out_path) as fh:
+            old = json.load(fh)
+    old.update(out)
+    with open(out_path, "w") as fh:
+        json.dump(old, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    print(json.dumps(out, indent=1))
+
+
+def measured_traffic(family, kernel, grid_y):
+    """DRAM bytes of one launch, or (None, why not)."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)[family]
+    except (OSError, ValueError, KeyError):
+        return None, "no ncu capture recorded"
+    if rec.get("sources") != sources_digest(family):
+        return None, "kernel sources changed since the capture"
+    gy = rec.get("grid", "").strip("()").split(",")
+    if rec.get("kernel") != kernel or len(gy) < 2 or int(gy[1]) != grid_y:
+        return None, f"capture is of {rec.get('kernel')} grid {rec.get('grid')}"
+    return rec["dram__bytes_read.sum"] + rec["dram__bytes_write.sum"], \
+        f"ncu capture of {kernel} grid {rec['grid']}: {rec['command']}"
+
+
+def launch_signature(family, tuning, chunk, groups):
+    """Template instance and grid.y of one float32 launch of an OSPR pass at H x W."""
+    cv, rv = tuning["col_variant"], tuning["row_variant"]
+    return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {cv}, 0>", chunk),
+            "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cv}, 0>", groups),
+            "ospr_row": (f"k_ospr_row<{W}, {rv}, 1, 0>", chunk)}.get(family, (None, None))
+
+
 # ------------------------------------------------------------------ our arm ----
 def run_ours(args):
     import torch
@@ -237,8 +319,11 @@ def run_ours(args):
     peak_bw = peaks["hbm_gbs"] if peaks else 6800.0
     bytes_dom = kernel_bytes(dom, P, chunk, groups, N_SF)
     achieved = bytes_dom / (ms_dom / n_dom / 1e3) / 1e9 if n_dom and bytes_dom else None
+    kname, grid_y = launch_signature(dom, tuning, chunk, groups)
+    traffic, traffic_src = measured_traffic(dom, kname, grid_y) if kname else (None, "no capture")
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
-                "frac": achieved / peak_bw if achieved else None, "traffic": None,
+                "frac": achieved / peak_bw if achieved else None, "traffic": traffic,
+                "traffic_source": traffic_src,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": bytes_dom,
                 "avg_launch_us": ms_dom / n_dom * 1e3 if n_dom else None,
@@ -630,7 +715,14 @@ def main():
     ap.add_argument("--learned", action="store_true", help="run the learned GS warm-start experiment")
     ap.add_argument("--learned-n", type=int, default=20000)
     ap.add_argument("--learned-epochs", type=int, default=2)
+    ap.add_argument("--record-traffic", default=None, metavar="CSV",
+                    help="store per-launch DRAM bytes from an ncu --csv log in profiles/dram_traffic.json")
+    ap.add_argument("--traffic-command", default="", help="the ncu command that wrote the CSV")
+    ap.add_argument("--traffic-out", default=TRAFFIC_FILE, help="where to store the records")
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.traffic_command, args.traffic_out)
+        return
     if args.learned:
         run_learned(args)
         return

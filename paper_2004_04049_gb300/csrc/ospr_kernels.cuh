@@ -132,17 +132,46 @@ __device__ __forceinline__ void row_line_fft(float2 (&v)[RowCfg<NR, V>::R], floa
 }
 
 // ------------------------------------------------------------------ pass 1 ----
-// Z for one column of one pair, in canonical layout (slot e <-> row t + T*e). MODE and
-// SINGLE are compile-time so that the element loops hold no branches: for each batch of
-// kBatch elements every load (target, mirror target, four codes) is issued before any
-// of them is used.
+// Z = E^h_{s0} + i E^h_{s1} needs, at pixel p, E_s(p) and E_s(-p) of both sub-frames, and
+// Z(-p) = conj(E^h_{s0}(p)) + i conj(E^h_{s1}(p)) needs the same four values. A CTA
+// therefore holds mirror columns together: its first LPC/2 lines take columns
+// u = blockIdx.x*LPC/2 + j and the last LPC/2 lines their mirrors W - u (for u = 0 the
+// self-mirrored columns 0 and W/2), and each element pair {p, -p} is generated once, by
+// one of the two threads that own p and -p, which hands the other its value through
+// shared memory.
+template <int LPC>
+__device__ __forceinline__ void mirror_column(int b, int lc, int W, int& col, int& partner) {
+    constexpr int HL = LPC / 2;
+    static_assert(LPC >= 2 && (LPC & (LPC - 1)) == 0, "mirror pairing needs an even power-of-two LPC");
+    const int u = b * HL + (lc & (HL - 1));
+    const bool second = lc >= HL;
+    if (u == 0) {
+        col = second ? W / 2 : 0;
+        partner = lc;
+    } else {
+        col = second ? W - u : u;
+        partner = second ? lc - HL : lc + HL;
+    }
+}
+
+// Element e of thread t is row r = t + T*e; its mirror row (H - r) mod H is row
+// (T - t) + T*(R-1-e) of thread T - t for t > 0 and row T*((R - e) mod R) of thread 0 for
+// t = 0. Threads with t > 0 generate slots 0..R/2-1 and receive R/2..R-1; thread 0
+// generates 0..R/2 (slots 0 and R/2 mirror onto themselves and are not handed over) and
+// receives R/2+1..R-1. `xline` is the partner line's buffer.
+//
+// MODE and SINGLE are compile-time so that the element loops hold no branches: for each
+// batch of kBatch elements every load (target, mirror target, four codes) is issued before
+// any of them is used. SINGLE (the last sub-frame of an odd N) has no mirror terms and
+// builds all R slots itself.
 constexpr int kBatch = 8;
 
 template <int NC, int V, int MODE, bool SINGLE>
 __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R], const OsprArgs& a,
-                                                  const float2* cs, int t, int c, int s0) {
+                                                  const float2* cs, float2* xline, int t, int c, int s0) {
     constexpr int R = ColCfg<NC, V>::R, T = NC / R;
-    constexpr int B = R < kBatch ? R : kBatch;
+    constexpr int EG = SINGLE ? R : R / 2;   // slots generated by every thread
+    constexpr int B = EG < kBatch ? EG : kBatch;
     const int W = a.W;
     const int cm = (W - c) & (W - 1);
     const int sh = a.ps.cs_shift;
@@ -165,10 +194,49 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
         z1 = fastmod_u32(d1.base_mod + uint32_t(cm), fm, L);
     }
     const int gshift = 64 - a.ps.bits;
+    // packed codes of (s0, p), (s0, -p), (s1, p), (s1, -p), one byte each, of row r (slot e)
+    auto codes_of = [&](int e, int r, int rm) -> uint32_t {
+        if constexpr (MODE == kPhaseTable) {
+            const uint32_t jm0 = (e == 0 && t == 0) ? z0 : m0;
+            const uint32_t jm1 = (e == 0 && t == 0) ? z1 : m1;
+            uint32_t w = __ldg(a.ps.codes + i0);
+            if constexpr (!SINGLE) {
+                w |= uint32_t(__ldg(a.ps.codes + jm0)) << 8;
+                w |= uint32_t(__ldg(a.ps.codes + i1)) << 16;
+                w |= uint32_t(__ldg(a.ps.codes + jm1)) << 24;
+            }
+            i0 += D; i0 -= (i0 >= L) ? L : 0u;
+            i1 += D; i1 -= (i1 >= L) ? L : 0u;
+            m0 = (m0 >= D) ? m0 - D : m0 + (L - D);
+            m1 = (m1 >= D) ? m1 - D : m1 + (L - D);
+            return w;
+        } else if constexpr (MODE == kPhaseGenerator) {
+            const uint64_t p = uint64_t(r) * uint64_t(W) + uint64_t(c);
+            const uint64_t pm = uint64_t(rm) * uint64_t(W) + uint64_t(cm);
+            uint32_t w = uint32_t(splitmix64_at(a.ps.seed, d0.base + p) >> gshift);
+            if constexpr (!SINGLE) {
+                w |= uint32_t(splitmix64_at(a.ps.seed, d0.base + pm) >> gshift) << 8;
+                w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + p) >> gshift) << 16;
+                w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + pm) >> gshift) << 24;
+            }
+            return w;
+        } else {
+            return 0u;   // flat phase
+        }
+    };
+    // Hermitian parts E(k) + conj(E(-k)) of both sub-frames at row r
+    auto hermitian = [&](float tp, float tm, uint32_t pk, float2& h0, float2& h1) {
+        const float2 c0 = cs_lookup(cs, (pk & 0xffu) << sh);
+        const float2 c0m = cs_lookup(cs, ((pk >> 8) & 0xffu) << sh);
+        const float2 c1 = cs_lookup(cs, ((pk >> 16) & 0xffu) << sh);
+        const float2 c1m = cs_lookup(cs, (pk >> 24) << sh);
+        h0 = make_float2(fmaf(tp, c0.x, tm * c0m.x), fmaf(tp, c0.y, -tm * c0m.y));
+        h1 = make_float2(fmaf(tp, c1.x, tm * c1m.x), fmaf(tp, c1.y, -tm * c1m.y));
+    };
 #pragma unroll
-    for (int e0 = 0; e0 < R; e0 += B) {
+    for (int e0 = 0; e0 < EG; e0 += B) {
         float tp[B], tm[B];
-        uint32_t pk[B];   // codes of (s0, p), (s0, -p), (s1, p), (s1, -p), one byte each
+        uint32_t pk[B];
 #pragma unroll
         for (int k = 0; k < B; ++k) {
             const int e = e0 + k;
@@ -176,48 +244,34 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
             const int rm = (NC - r) & (NC - 1);
             tp[k] = __ldg(a.target + r * W + c);
             tm[k] = SINGLE ? 0.f : __ldg(a.target + rm * W + cm);
-            if constexpr (MODE == kPhaseTable) {
-                const uint32_t jm0 = (e == 0 && t == 0) ? z0 : m0;
-                const uint32_t jm1 = (e == 0 && t == 0) ? z1 : m1;
-                uint32_t w = __ldg(a.ps.codes + i0);
-                if constexpr (!SINGLE) {
-                    w |= uint32_t(__ldg(a.ps.codes + jm0)) << 8;
-                    w |= uint32_t(__ldg(a.ps.codes + i1)) << 16;
-                    w |= uint32_t(__ldg(a.ps.codes + jm1)) << 24;
-                }
-                pk[k] = w;
-                i0 += D; i0 -= (i0 >= L) ? L : 0u;
-                i1 += D; i1 -= (i1 >= L) ? L : 0u;
-                m0 = (m0 >= D) ? m0 - D : m0 + (L - D);
-                m1 = (m1 >= D) ? m1 - D : m1 + (L - D);
-            } else if constexpr (MODE == kPhaseGenerator) {
-                const uint64_t p = uint64_t(r) * uint64_t(W) + uint64_t(c);
-                const uint64_t pm = uint64_t(rm) * uint64_t(W) + uint64_t(cm);
-                uint32_t w = uint32_t(splitmix64_at(a.ps.seed, d0.base + p) >> gshift);
-                if constexpr (!SINGLE) {
-                    w |= uint32_t(splitmix64_at(a.ps.seed, d0.base + pm) >> gshift) << 8;
-                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + p) >> gshift) << 16;
-                    w |= uint32_t(splitmix64_at(a.ps.seed, d1.base + pm) >> gshift) << 24;
-                }
-                pk[k] = w;
-            } else {
-                pk[k] = 0u;   // flat phase
-            }
+            pk[k] = codes_of(e, r, rm);
         }
 #pragma unroll
         for (int k = 0; k < B; ++k) {
-            const float2 c0 = cs_lookup(cs, (pk[k] & 0xffu) << sh);
+            const int e = e0 + k;
             if constexpr (SINGLE) {
-                v[e0 + k] = make_float2(tp[k] * c0.x, tp[k] * c0.y);
+                const float2 c0 = cs_lookup(cs, (pk[k] & 0xffu) << sh);
+                v[e] = make_float2(tp[k] * c0.x, tp[k] * c0.y);
             } else {
-                const float2 c0m = cs_lookup(cs, ((pk[k] >> 8) & 0xffu) << sh);
-                const float2 c1 = cs_lookup(cs, ((pk[k] >> 16) & 0xffu) << sh);
-                const float2 c1m = cs_lookup(cs, (pk[k] >> 24) << sh);
-                // Hermitian parts E(k) + conj(E(-k)) of both sub-frames, packed as a + i b
-                const float2 h0 = make_float2(fmaf(tp[k], c0.x, tm[k] * c0m.x), fmaf(tp[k], c0.y, -tm[k] * c0m.y));
-                const float2 h1 = make_float2(fmaf(tp[k], c1.x, tm[k] * c1m.x), fmaf(tp[k], c1.y, -tm[k] * c1m.y));
-                v[e0 + k] = make_float2(h0.x - h1.y, h0.y + h1.x);
+                float2 h0, h1;
+                hermitian(tp[k], tm[k], pk[k], h0, h1);
+                v[e] = make_float2(h0.x - h1.y, h0.y + h1.x);
+                if (t > 0 || e > 0) {
+                    const int rm = (NC - (t + T * e)) & (NC - 1);
+                    xline[pad_index<R>(rm)] = make_float2(h0.x + h1.y, h1.x - h0.y);
+                }
             }
+        }
+    }
+    if constexpr (!SINGLE) {
+        if (t == 0) {   // row H/2: its mirror is row H/2 of the partner line, built there
+            constexpr int e = R / 2;
+            const int r = T * e;
+            const float tp = __ldg(a.target + r * W + c);
+            const float tm = __ldg(a.target + r * W + cm);
+            float2 h0, h1;
+            hermitian(tp, tm, codes_of(e, r, r), h0, h1);
+            v[e] = make_float2(h0.x - h1.y, h0.y + h1.x);
         }
     }
 }
@@ -225,7 +279,8 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
 template <int NC, int V, int PREC>
 __global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
 k_ospr_col_ifft(OsprArgs a) {
-    constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R;
+    constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R, S = col_stride<NC, V>();
+    static_assert(stage_count(NC, R) > 1, "the line FFT's opening barrier guards the exchange buffer");
     extern __shared__ float2 sm[];
     float2* cs = sm;
     float2* lines = sm + kCsSmemEntries;
@@ -234,19 +289,28 @@ k_ospr_col_ifft(OsprArgs a) {
 
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
-    const int c = blockIdx.x * LPC + lc;
+    int c, pl;
+    mirror_column<LPC>(blockIdx.x, lc, W, c, pl);
     const int s0 = 2 * (a.first_pair + int(blockIdx.y));
-    const bool single = s0 + 1 >= a.N;
+    const bool single = s0 + 1 >= a.N;   // uniform over the CTA
+    float2* xline = lines + pl * S;
     float2 v[R];
     if (a.ps.mode == kPhaseTable) {
-        if (single) ospr_build_column<NC, V, kPhaseTable, true>(v, a, cs, t, c, s0);
-        else ospr_build_column<NC, V, kPhaseTable, false>(v, a, cs, t, c, s0);
+        if (single) ospr_build_column<NC, V, kPhaseTable, true>(v, a, cs, xline, t, c, s0);
+        else ospr_build_column<NC, V, kPhaseTable, false>(v, a, cs, xline, t, c, s0);
     } else if (a.ps.mode == kPhaseGenerator) {
-        if (single) ospr_build_column<NC, V, kPhaseGenerator, true>(v, a, cs, t, c, s0);
-        else ospr_build_column<NC, V, kPhaseGenerator, false>(v, a, cs, t, c, s0);
+        if (single) ospr_build_column<NC, V, kPhaseGenerator, true>(v, a, cs, xline, t, c, s0);
+        else ospr_build_column<NC, V, kPhaseGenerator, false>(v, a, cs, xline, t, c, s0);
     } else {
-        if (single) ospr_build_column<NC, V, kPhaseFlat, true>(v, a, cs, t, c, s0);
-        else ospr_build_column<NC, V, kPhaseFlat, false>(v, a, cs, t, c, s0);
+        if (single) ospr_build_column<NC, V, kPhaseFlat, true>(v, a, cs, xline, t, c, s0);
+        else ospr_build_column<NC, V, kPhaseFlat, false>(v, a, cs, xline, t, c, s0);
+    }
+    if (!single) {
+        __syncthreads();
+        const float2* own = lines + lc * S;
+#pragma unroll
+        for (int e = R / 2; e < R; ++e)
+            if (t > 0 || e > R / 2) v[e] = own[pad_index<R>(t + T * e)];
     }
     col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
     float2* z = a.zbuf + size_t(blockIdx.y) * size_t(NC) * size_t(W);
