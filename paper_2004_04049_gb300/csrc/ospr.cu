@@ -52,14 +52,23 @@ __global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, 
 }
 
 // ------------------------------------------------------------------- host ----
-// Per-shape tuning: tile variants of the column and row passes, pairs in flight (chunk)
-// and partial accumulators (groups). Defaults: variant 0, 16 pairs, 4 groups (overridable
-// with HOLO_OSPR_CHUNK / HOLO_OSPR_GROUPS); ospr_autotune replaces them per shape with
-// the fastest measured candidate, and HOLO_TUNE_CACHE names a file that keeps the choices
-// across processes. The workspace size follows the tuning of the shape.
+// Per-shape tuning: tile variants of the three passes (column IDFT, row, column DFT;
+// the two column passes share only the field layout, so their tiles are independent),
+// pairs in flight (chunk) and partial accumulators (groups). Defaults: variant 0, 16
+// pairs, 4 groups (overridable with HOLO_OSPR_CHUNK / HOLO_OSPR_GROUPS); ospr_autotune
+// replaces them per shape with the fastest measured candidate, and HOLO_TUNE_CACHE names
+// a file that keeps the choices across processes. The workspace size follows the tuning
+// of the shape.
 struct OsprTuning {
-    int col_v, row_v, chunk, groups;
+    int ci_v, cf_v, row_v, chunk, groups;
 };
+
+static OsprTuning clamp_variants(int H, int W, OsprTuning t) {
+    if (t.ci_v < 0 || t.ci_v >= col_variants(H)) t.ci_v = 0;
+    if (t.cf_v < 0 || t.cf_v >= col_variants(H)) t.cf_v = 0;
+    if (t.row_v < 0 || t.row_v >= row_variants(W)) t.row_v = 0;
+    return t;
+}
 
 static int env_int(const char* name, int lo, int hi, int dflt) {
     const char* v = getenv(name);
@@ -69,7 +78,7 @@ static int env_int(const char* name, int lo, int hi, int dflt) {
 }
 
 static OsprTuning default_tuning() {
-    static const OsprTuning t{0, 0, env_int("HOLO_OSPR_CHUNK", 1, kMaxChunkPairs, kMaxChunkPairs),
+    static const OsprTuning t{0, 0, 0, env_int("HOLO_OSPR_CHUNK", 1, kMaxChunkPairs, kMaxChunkPairs),
                               env_int("HOLO_OSPR_GROUPS", 1, kMaxGroups, kMaxGroups)};
     return t;
 }
@@ -85,12 +94,12 @@ static void tune_cache_load_locked() {
     if (!path || !*path) return;
     FILE* f = fopen(path, "r");
     if (!f) return;
-    int H, W, cv, rv, ch, gr;
-    while (fscanf(f, " {\"H\": %d, \"W\": %d, \"col_variant\": %d, \"row_variant\": %d, \"chunk\": %d, "
-                     "\"groups\": %d}", &H, &W, &cv, &rv, &ch, &gr) == 6) {
-        if (cv < 0 || cv > 1 || rv < 0 || rv > 1 || ch < 1 || ch > kMaxChunkPairs || gr < 1 || gr > kMaxGroups)
-            continue;
-        g_tune[{H, W}] = OsprTuning{has_variant(H) ? cv : 0, has_variant(W) ? rv : 0, ch, gr};
+    int H, W, ci, cf, rv, ch, gr;
+    while (fscanf(f, " {\"H\": %d, \"W\": %d, \"col_ifft_variant\": %d, \"col_fft_variant\": %d, "
+                     "\"row_variant\": %d, \"chunk\": %d, \"groups\": %d}",
+                  &H, &W, &ci, &cf, &rv, &ch, &gr) == 7) {
+        if (ch < 1 || ch > kMaxChunkPairs || gr < 1 || gr > kMaxGroups) continue;
+        g_tune[{H, W}] = clamp_variants(H, W, OsprTuning{ci, cf, rv, ch, gr});
     }
     fclose(f);
 }
@@ -101,9 +110,9 @@ static void tune_cache_save_locked() {
     FILE* f = fopen(path, "w");
     if (!f) return;
     for (const auto& kv : g_tune)
-        fprintf(f, "{\"H\": %d, \"W\": %d, \"col_variant\": %d, \"row_variant\": %d, \"chunk\": %d, "
-                   "\"groups\": %d}\n", kv.first.first, kv.first.second, kv.second.col_v, kv.second.row_v,
-                kv.second.chunk, kv.second.groups);
+        fprintf(f, "{\"H\": %d, \"W\": %d, \"col_ifft_variant\": %d, \"col_fft_variant\": %d, "
+                   "\"row_variant\": %d, \"chunk\": %d, \"groups\": %d}\n", kv.first.first, kv.first.second,
+                kv.second.ci_v, kv.second.cf_v, kv.second.row_v, kv.second.chunk, kv.second.groups);
     fclose(f);
 }
 
@@ -122,7 +131,7 @@ static void tuning_install(int H, int W, const OsprTuning& t, bool save) {
 }
 
 struct OsprPlan {
-    int npairs, chunk, groups, col_v, row_v;
+    int npairs, chunk, groups, ci_v, cf_v, row_v;
     int prec = HOLO_FP32;
     size_t z_bytes, s_bytes, total;
 };
@@ -133,8 +142,10 @@ static OsprPlan ospr_plan_with(int H, int W, int N, const OsprTuning& t) {
     pl.npairs = (N + 1) / 2;
     pl.chunk = pl.npairs < t.chunk ? pl.npairs : t.chunk;
     pl.groups = pl.chunk < t.groups ? pl.chunk : t.groups;
-    pl.col_v = has_variant(H) ? t.col_v : 0;
-    pl.row_v = has_variant(W) ? t.row_v : 0;
+    const OsprTuning c = clamp_variants(H, W, t);
+    pl.ci_v = c.ci_v;
+    pl.cf_v = c.cf_v;
+    pl.row_v = c.row_v;
     pl.z_bytes = align_up(size_t(pl.chunk) * P * sizeof(float2), 256);
     pl.s_bytes = align_up(size_t(pl.groups) * P * sizeof(float), 256);
     pl.total = pl.z_bytes + pl.s_bytes;
@@ -147,7 +158,7 @@ static bool tc_shape(int H, int W) { return (H == 1024 || H == 2048) && (W == 10
 static OsprPlan ospr_plan(int H, int W, int N, int precision = HOLO_FP32) {
     OsprTuning t = tuning_for(H, W);
     if (precision != HOLO_FP32) {
-        t.col_v = kTcColVariant;
+        t.ci_v = t.cf_v = kTcColVariant;
         t.row_v = kTcRowVariant;
     }
     OsprPlan pl = ospr_plan_with(H, W, N, t);
@@ -186,9 +197,9 @@ static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_repla
         a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
         a.accumulate = first > 0;
         if (pl.prec == HOLO_FP32) {
-            if ((rc = ospr_run_col_ifft(a, pl.col_v, st))) return rc;
+            if ((rc = ospr_run_col_ifft(a, pl.ci_v, st))) return rc;
             if ((rc = ospr_run_row(a, pl.row_v, replay, st))) return rc;
-            if (replay && (rc = ospr_run_col_fft(a, pl.col_v, st))) return rc;
+            if (replay && (rc = ospr_run_col_fft(a, pl.cf_v, st))) return rc;
         } else {
             if ((rc = ospr_run_col_ifft_tc(a, pl.prec, st))) return rc;
             if ((rc = ospr_run_row_tc(a, pl.prec, replay, st))) return rc;
@@ -274,29 +285,34 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     return HOLO_OK;
 }
 
-extern "C" int ospr_tuning_get(int H, int W, int* col_variant, int* row_variant, int* chunk, int* groups) {
+extern "C" int ospr_tuning_get(int H, int W, int* col_ifft_variant, int* col_fft_variant, int* row_variant,
+                               int* chunk, int* groups) {
     clear_error();
     int rc = check_shape("ospr_tuning_get", H, W);
     if (rc) return rc;
-    if (!col_variant || !row_variant || !chunk || !groups) return fail(HOLO_EINVAL, "ospr_tuning_get: NULL output");
-    const OsprTuning t = tuning_for(H, W);
-    *col_variant = has_variant(H) ? t.col_v : 0;
-    *row_variant = has_variant(W) ? t.row_v : 0;
+    if (!col_ifft_variant || !col_fft_variant || !row_variant || !chunk || !groups)
+        return fail(HOLO_EINVAL, "ospr_tuning_get: NULL output");
+    const OsprTuning t = clamp_variants(H, W, tuning_for(H, W));
+    *col_ifft_variant = t.ci_v;
+    *col_fft_variant = t.cf_v;
+    *row_variant = t.row_v;
     *chunk = t.chunk;
     *groups = t.groups;
     return HOLO_OK;
 }
 
-extern "C" int ospr_tuning_set(int H, int W, int col_variant, int row_variant, int chunk, int groups) {
+extern "C" int ospr_tuning_set(int H, int W, int col_ifft_variant, int col_fft_variant, int row_variant,
+                               int chunk, int groups) {
     clear_error();
     int rc = check_shape("ospr_tuning_set", H, W);
     if (rc) return rc;
-    if (col_variant < 0 || col_variant > 1 || row_variant < 0 || row_variant > 1 || chunk < 1 ||
-        chunk > kMaxChunkPairs || groups < 1 || groups > kMaxGroups)
-        return fail(HOLO_EINVAL, "ospr_tuning_set: variants 0..1, chunk 1..%d, groups 1..%d", kMaxChunkPairs,
-                    kMaxGroups);
-    tuning_install(H, W, OsprTuning{has_variant(H) ? col_variant : 0, has_variant(W) ? row_variant : 0, chunk,
-                                    groups}, false);
+    if (col_ifft_variant < 0 || col_ifft_variant > 2 || col_fft_variant < 0 || col_fft_variant > 2 ||
+        row_variant < 0 || row_variant > 1 || chunk < 1 || chunk > kMaxChunkPairs || groups < 1 ||
+        groups > kMaxGroups)
+        return fail(HOLO_EINVAL, "ospr_tuning_set: column variants 0..2, row variant 0..1, chunk 1..%d, groups 1..%d",
+                    kMaxChunkPairs, kMaxGroups);
+    tuning_install(H, W, clamp_variants(H, W, OsprTuning{col_ifft_variant, col_fft_variant, row_variant, chunk,
+                                                         groups}), false);
     return HOLO_OK;
 }
 
@@ -310,7 +326,7 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
     const size_t P = size_t(H) * W;
     const int64_t L = 10007;
     // the largest candidate plan bounds the workspace
-    const size_t ws_bytes = ospr_plan_with(H, W, N, OsprTuning{0, 0, kMaxChunkPairs, kMaxGroups}).total;
+    const size_t ws_bytes = ospr_plan_with(H, W, N, OsprTuning{0, 0, 0, kMaxChunkPairs, kMaxGroups}).total;
     void *d_t = nullptr, *d_codes = nullptr, *d_bits = nullptr, *d_rep = nullptr, *d_ws = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaMalloc(&d_t, P * sizeof(float));
@@ -357,26 +373,36 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
         *ms = v[reps / 2];
         return HOLO_OK;
     };
-    OsprTuning best{0, 0, kMaxChunkPairs < npairs ? kMaxChunkPairs : npairs, kMaxGroups};
+    OsprTuning best{0, 0, 0, kMaxChunkPairs < npairs ? kMaxChunkPairs : npairs, kMaxGroups};
     float best_t = 0.f;
     if (!rc) rc = measure(best, &best_t);
-    // coordinate descent over tile variants, pairs in flight, accumulator groups
+    // coordinate descent, two sweeps: column IDFT tiles, row tiles, column DFT tiles,
+    // pairs in flight, accumulator groups (a tile choice can change the best chunking)
     auto consider = [&](OsprTuning t) {
         if (rc) return;
         float ms = 0.f;
         rc = measure(t, &ms);
         if (!rc && ms < best_t) { best_t = ms; best = t; }
     };
-    if (has_variant(H)) { OsprTuning t = best; t.col_v = 1; consider(t); }
-    if (has_variant(W)) { OsprTuning t = best; t.row_v = 1; consider(t); }
     const int chunks[] = {2, 4, 8, 12, 16};
-    const OsprTuning base = best;
-    for (int c : chunks)
-        if (c < npairs && c != base.chunk) { OsprTuning t = base; t.chunk = c; consider(t); }
-    const OsprTuning base2 = best;
     const int groups[] = {1, 2, 4};
-    for (int g : groups)
-        if (g != base2.groups && g <= base2.chunk) { OsprTuning t = base2; t.groups = g; consider(t); }
+    for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
+        OsprTuning b = best;
+        for (int v = 0; v < col_variants(H); ++v)
+            if (v != b.ci_v) { OsprTuning t = b; t.ci_v = v; consider(t); }
+        b = best;
+        for (int v = 0; v < row_variants(W); ++v)
+            if (v != b.row_v) { OsprTuning t = b; t.row_v = v; consider(t); }
+        b = best;
+        for (int v = 0; v < col_variants(H); ++v)
+            if (v != b.cf_v) { OsprTuning t = b; t.cf_v = v; consider(t); }
+        b = best;
+        for (int c : chunks)
+            if (c <= npairs && c != b.chunk) { OsprTuning t = b; t.chunk = c; consider(t); }
+        b = best;
+        for (int g : groups)
+            if (g != b.groups && g <= b.chunk) { OsprTuning t = b; t.groups = g; consider(t); }
+    }
     release();
     if (rc) {
         tuning_install(H, W, before, false);
@@ -430,7 +456,8 @@ static bool noalloc_plan(int H, int W, int N, OsprPlan* pl) {
     pl->chunk = chunk;
     pl->z_bytes = align_up(size_t(chunk) * P * sizeof(float2), 256);
     pl->total = pl->z_bytes + pl->s_bytes;
-    pl->col_v = 0;
+    pl->ci_v = 0;
+    pl->cf_v = 0;
     pl->row_v = 0;
     return pl->total <= size_t(HOLO_NOALLOC_SCRATCH_BYTES);
 }

@@ -28,15 +28,17 @@ static int launch_col_fft(const OsprArgs& a, cudaStream_t st) {
     return ln.done("ospr_col_fft launch");
 }
 
+#define HOLO_COL_VARIANTS(N, v, F) \
+    (v == 2 ? F<N, 2>(a, st) : v == 1 ? F<N, 1>(a, st) : F<N, 0>(a, st))
 #define HOLO_COL_SWITCH(n, v, F)                                              \
     switch (n) {                                                              \
         case 64: return F<64, 0>(a, st);                                      \
         case 128: return F<128, 0>(a, st);                                    \
         case 256: return F<256, 0>(a, st);                                    \
-        case 512: return v ? F<512, 1>(a, st) : F<512, 0>(a, st);             \
-        case 1024: return v ? F<1024, 1>(a, st) : F<1024, 0>(a, st);          \
-        case 2048: return v ? F<2048, 1>(a, st) : F<2048, 0>(a, st);          \
-        case 4096: return v ? F<4096, 1>(a, st) : F<4096, 0>(a, st);          \
+        case 512: return HOLO_COL_VARIANTS(512, v, F);                        \
+        case 1024: return HOLO_COL_VARIANTS(1024, v, F);                      \
+        case 2048: return HOLO_COL_VARIANTS(2048, v, F);                      \
+        case 4096: return HOLO_COL_VARIANTS(4096, v, F);                      \
         default: return fail(HOLO_EUNSUPPORTED, "column length %d", n);      \
     }
 

@@ -44,6 +44,10 @@ template <> struct ColCfg<512, 1>  { static constexpr int R = 32, LPC = 16; };
 template <> struct ColCfg<1024, 1> { static constexpr int R = 32, LPC = 8; };
 template <> struct ColCfg<2048, 1> { static constexpr int R = 32, LPC = 4; };
 template <> struct ColCfg<4096, 1> { static constexpr int R = 32, LPC = 2; };
+template <> struct ColCfg<512, 2>  { static constexpr int R = 16, LPC = 8; };
+template <> struct ColCfg<1024, 2> { static constexpr int R = 16, LPC = 8; };
+template <> struct ColCfg<2048, 2> { static constexpr int R = 16, LPC = 4; };
+template <> struct ColCfg<4096, 2> { static constexpr int R = 16, LPC = 2; };
 template <int N, int V> struct RowCfg;
 template <> struct RowCfg<64, 0>   { static constexpr int R = 2,  LPR = 4; };
 template <> struct RowCfg<128, 0>  { static constexpr int R = 4,  LPR = 4; };
@@ -56,8 +60,9 @@ template <> struct RowCfg<512, 1>  { static constexpr int R = 8,  LPR = 4; };
 template <> struct RowCfg<1024, 1> { static constexpr int R = 16, LPR = 2; };
 template <> struct RowCfg<2048, 1> { static constexpr int R = 16, LPR = 1; };
 template <> struct RowCfg<4096, 1> { static constexpr int R = 16, LPR = 1; };
-// lengths with a second tile variant
-constexpr bool has_variant(int N) { return N >= 512; }
+// tile variants of each length (column passes: 0..2, row pass: 0..1 from 512 up)
+constexpr int col_variants(int N) { return N >= 512 ? 3 : 1; }
+constexpr int row_variants(int N) { return N >= 512 ? 2 : 1; }
 
 constexpr int kMaxChunkPairs = 16;   // pairs whose fields are in flight at once
 constexpr int kMaxGroups = 4;        // partial accumulators of the column DFT pass
@@ -164,7 +169,7 @@ __device__ __forceinline__ void mirror_column(int b, int lc, int W, int& col, in
 // batch of kBatch elements every load (target, mirror target, four codes) is issued before
 // any of them is used. SINGLE (the last sub-frame of an odd N) has no mirror terms and
 // builds all R slots itself.
-constexpr int kBatch = 8;
+constexpr int kBatch = 16;
 
 template <int NC, int V, int MODE, bool SINGLE>
 __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R], const OsprArgs& a,

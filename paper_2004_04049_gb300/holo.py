@@ -83,8 +83,8 @@ _SIGS = {
     "holo_graph_launch": (_c.c_int, [_c.c_void_p, _c.c_void_p]),
     "holo_graph_destroy": (_c.c_int, [_c.c_void_p]),
     "ospr_autotune": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.POINTER(_c.c_double)]),
-    "ospr_tuning_get": (_c.c_int, [_c.c_int, _c.c_int] + [_c.POINTER(_c.c_int)] * 4),
-    "ospr_tuning_set": (_c.c_int, [_c.c_int] * 6),
+    "ospr_tuning_get": (_c.c_int, [_c.c_int, _c.c_int] + [_c.POINTER(_c.c_int)] * 5),
+    "ospr_tuning_set": (_c.c_int, [_c.c_int] * 7),
     "gs_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "gs_iterate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
                               _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
@@ -281,13 +281,14 @@ def ospr_autotune(H, W, N, reps=3, stream=None):
 
 
 def ospr_tuning_get(H, W):
-    v = [ctypes.c_int(0) for _ in range(4)]
+    v = [ctypes.c_int(0) for _ in range(5)]
     _call("ospr_tuning_get", H, W, *[ctypes.byref(x) for x in v])
-    return {"col_variant": v[0].value, "row_variant": v[1].value, "chunk": v[2].value, "groups": v[3].value}
+    return {"col_ifft_variant": v[0].value, "col_fft_variant": v[1].value, "row_variant": v[2].value,
+            "chunk": v[3].value, "groups": v[4].value}
 
 
-def ospr_tuning_set(H, W, col_variant=0, row_variant=0, chunk=16, groups=4):
-    return _call("ospr_tuning_set", H, W, col_variant, row_variant, chunk, groups)
+def ospr_tuning_set(H, W, col_ifft_variant=0, col_fft_variant=0, row_variant=0, chunk=16, groups=4):
+    return _call("ospr_tuning_set", H, W, col_ifft_variant, col_fft_variant, row_variant, chunk, groups)
 
 
 def gs_workspace_size(H, W, iters, precision=HOLO_FP32):

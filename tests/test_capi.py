@@ -92,3 +92,24 @@ def test_batch_workspace_is_host_only(lib):
     with pytest.raises(holo.HoloError) as ei:
         holo.ospr_batch_workspace_size(bad)
     assert "frame 0" in str(ei.value)
+
+
+def test_tuning_set_get_host_only(lib):
+    # 256-point columns have one tile variant: column variants fall back to 0; 512-point
+    # rows keep variant 1
+    holo.ospr_tuning_set(256, 512, 2, 1, 1, 5, 3)
+    try:
+        t = holo.ospr_tuning_get(256, 512)
+        assert t == {"col_ifft_variant": 0, "col_fft_variant": 0, "row_variant": 1, "chunk": 5, "groups": 3}
+        holo.ospr_tuning_set(1024, 1024, 2, 1, 0, 12, 2)
+        t = holo.ospr_tuning_get(1024, 1024)
+        assert (t["col_ifft_variant"], t["col_fft_variant"], t["chunk"], t["groups"]) == (2, 1, 12, 2)
+        # the workspace follows the setting: 12 complex64 fields and 2 float32 accumulators
+        assert holo.ospr_workspace_size(1024, 1024, 24) == 12 * 8 * 2**20 + 2 * 4 * 2**20
+        for bad in [(3, 0, 0, 4, 1), (0, -1, 0, 4, 1), (0, 0, 2, 4, 1), (0, 0, 0, 17, 1), (0, 0, 0, 4, 5)]:
+            with pytest.raises(holo.HoloError) as ei:
+                holo.ospr_tuning_set(1024, 1024, *bad)
+            assert ei.value.status == holo.HOLO_EINVAL
+    finally:
+        holo.ospr_tuning_set(256, 512)
+        holo.ospr_tuning_set(1024, 1024)

@@ -17,7 +17,8 @@ from synthetic import blob_target
 
 pytestmark = pytest.mark.gpu
 
-SETTINGS = [(1, 0, 16, 4), (0, 1, 16, 4), (1, 1, 2, 1), (1, 1, 3, 2), (0, 0, 1, 1)]
+# (column IDFT variant, column DFT variant, row variant, chunk, groups)
+SETTINGS = [(1, 1, 0, 16, 4), (0, 0, 1, 16, 4), (2, 1, 1, 2, 1), (1, 2, 1, 3, 2), (2, 2, 0, 5, 3), (0, 0, 0, 1, 1)]
 _ORACLE = {}
 
 
@@ -59,11 +60,12 @@ def test_autotune_installs_and_records(cuda, tmp_path):
     finally:
         os.environ.pop("HOLO_TUNE_CACHE", None)
     assert ms > 0.0
-    assert t["col_variant"] in (0, 1) and t["row_variant"] in (0, 1)
+    assert t["col_ifft_variant"] in (0, 1, 2) and t["col_fft_variant"] in (0, 1, 2) and t["row_variant"] in (0, 1)
     assert 1 <= t["chunk"] <= 16 and 1 <= t["groups"] <= min(4, t["chunk"])
     rows = [json.loads(x) for x in path.read_text().splitlines()]
     rec = [r for r in rows if r["H"] == 512 and r["W"] == 1024]
-    assert rec and rec[0]["chunk"] == t["chunk"] and rec[0]["col_variant"] == t["col_variant"]
+    assert rec and rec[0]["chunk"] == t["chunk"] and rec[0]["col_ifft_variant"] == t["col_ifft_variant"]
+    assert rec[0]["col_fft_variant"] == t["col_fft_variant"] and rec[0]["row_variant"] == t["row_variant"]
     # the tuned setting still computes the same bits as the default one, up to ties
     T = blob_target(512, 1024, 1201)
     tt = torch.from_numpy(T).to(cuda)
