@@ -5,14 +5,18 @@ per frame, one frame for each table length L in 2^8 .. 2^20 plus the unrepeated
 generator (14 frames, 336 sub-frames), alternating seeded blob and band-limited-noise
 targets. Each frame runs the whole hot path through the C ABI: lut_build ->
 ospr_generate (LUT-apply, back-propagation IDFT, binarise, replay DFT, accumulate) ->
-replay_error. GS (1024x1024, 20 iterations, 256 levels, LUT-random start, L = 10007)
-is timed in the same run and reported beside it.
+replay_error. The frames are independent, so the step is one ospr_generate_batch call
+(the library runs them concurrently on its internal streams); the same step made of
+per-frame calls on one stream is timed too ("sequential"). GS (1024x1024, 20
+iterations, 256 levels, LUT-random start, L = 10007) is timed in the same run and
+reported beside it.
 
 Timing: W warm-up steps, then K steps each bracketed by CUDA events on the launching
 stream; L2 is flushed (a 512 MiB write) before every timed step, outside the events.
 The dominant kernel's duration comes from the library's own CUDA-event profiling of
-every launch in the timed steps. `--impl reference` times the float64 CPU oracle on
-the host cores instead (a bounded sample of the same workload).
+every launch in the sequential leg's timed steps, where kernels run one at a time.
+`--impl reference` times the float64 CPU oracle on the host cores instead (a bounded
+sample of the same workload).
 """
 
 import argparse
@@ -133,8 +137,6 @@ def kernel_bytes(family, P, pairs, groups, N):
         return groups * 4 * P + 4 * P
     if family in ("err_pass1", "err_pass2"):
         return 8 * P
-    if family == "err_finish":
-        return 0
     if family == "lut_build":
         return 0
     return None
@@ -221,9 +223,9 @@ def measured_traffic(family, kernel, grid_y):
 
 def launch_signature(family, tuning, chunk, groups):
     """Template instance and grid.y of one float32 launch of an OSPR pass at H x W."""
-    cv, rv = tuning["col_variant"], tuning["row_variant"]
-    return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {cv}, 0>", chunk),
-            "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cv}, 0>", groups),
+    ci, cf, rv = tuning["col_ifft_variant"], tuning["col_fft_variant"], tuning["row_variant"]
+    return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {ci}, 0>", chunk),
+            "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cf}, 0>", groups),
             "ospr_row": (f"k_ospr_row<{W}, {rv}, 1, 0>", chunk)}.get(family, (None, None))
 
 
@@ -246,69 +248,96 @@ def run_ours(args):
 
     targets = [torch.from_numpy(blob_target(H, W, 1000 + rank)).to(dev),
                torch.from_numpy(noise_target(H, W, 2000 + rank)).to(dev)]
-    maxL = max(L_SWEEP)
-    codes = torch.empty(maxL, dtype=torch.uint8, device=dev)
+    nfr = len(L_SWEEP)
+    # every frame of the step has its own table, target copy and outputs, so the frames
+    # are independent and one ospr_generate_batch call runs them all
+    fr = []
+    for i, L in enumerate(L_SWEEP):
+        fr.append({"L": L, "T": targets[i % 2].clone(),
+                   "codes": torch.empty(max(L, 1), dtype=torch.uint8, device=dev),
+                   "bits": torch.empty((N_SF, P // 32), dtype=torch.int32, device=dev),
+                   "I": torch.empty((H, W), dtype=torch.float32, device=dev),
+                   "err": torch.empty(3, dtype=torch.float64, device=dev)})
+    descs = [holo.frame_desc(f["T"], H, W, N_SF, f["codes"] if f["L"] > 0 else None, f["L"], 256, LUT_SEED,
+                             f["L"] > 0, 0, 0, f["bits"], f["I"], f["err"]) for f in fr]
+    arr = holo.frame_array(descs)
     ews = torch.empty(holo.replay_error_workspace_size(H, W), dtype=torch.uint8, device=dev)
-    bits = torch.empty((N_SF, P // 32), dtype=torch.int32, device=dev)
-    replay = torch.empty((H, W), dtype=torch.float32, device=dev)
-    errs = torch.empty((len(L_SWEEP), 3), dtype=torch.float64, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s = stream.cuda_stream
 
-    def frame(i, L, tgt):
-        if L > 0:
-            holo.lut_build(LUT_SEED, L, 256, codes, None, stream=stream.cuda_stream)
-        pipeline.ospr(tgt, N_SF, codes if L > 0 else None, L, 256, LUT_SEED, 0, 0,
-                      ws=ws, out_bits=bits, out_replay=replay, stream=stream.cuda_stream)
-        pipeline.error(replay, tgt, ws=ews, out=errs[i], stream=stream.cuda_stream)
+    def step_batch():
+        holo.ospr_generate_batch(arr, holo.HOLO_FP32, bws, stream=s)
 
-    def step():
-        for i, L in enumerate(L_SWEEP):
-            frame(i, L, targets[i % 2])
+    def frame(f):
+        if f["L"] > 0:
+            holo.lut_build(LUT_SEED, f["L"], 256, f["codes"], None, stream=s)
+        pipeline.ospr(f["T"], N_SF, f["codes"] if f["L"] > 0 else None, f["L"], 256, LUT_SEED, 0, 0,
+                      ws=ws, out_bits=f["bits"], out_replay=f["I"], stream=s)
+        pipeline.error(f["I"], f["T"], ws=ews, out=f["err"], stream=s)
+
+    def step_sequential():
+        for f in fr:
+            frame(f)
 
     def barrier():
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
 
+    def timed_steps(fn, k, profile=False):
+        """k steps, L2 flushed before each (outside the events); per-step ms."""
+        if profile:
+            holo.holo_profile_reset()
+            holo.holo_profile_enable(True)
+        times = []
+        for _ in range(k):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            times.append((e0, e1))
+        barrier()
+        if profile:
+            holo.holo_profile_enable(False)
+        return [a.elapsed_time(b) for a, b in times]
+
     # FFT tile variants and chunking for this shape, picked by the library's autotuner
-    tune_ms = holo.ospr_autotune(H, W, N_SF, reps=3, stream=stream.cuda_stream) if not args.no_tune else None
+    tune_ms = holo.ospr_autotune(H, W, N_SF, reps=3, stream=s) if not args.no_tune else None
     tuning = holo.ospr_tuning_get(H, W)
     ws = torch.empty(holo.ospr_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
+    bws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=dev)
 
+    # headline: the 14-frame step as one batch call (frames concurrent on internal streams)
     for _ in range(args.warmup):
-        step()
+        step_batch()
     barrier()
-
-    holo.holo_profile_reset()
     launches0 = holo.holo_launch_count()
     sampler = ClockSampler(local)
     sampler.start()
-    holo.holo_profile_enable(True)
-    times = []
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        times.append((e0, e1))
-    barrier()
-    holo.holo_profile_enable(False)
+    step_ms = timed_steps(step_batch, args.steps)
     clocks = sampler.stop()
     launches = holo.holo_launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in times]
     total_ms = float(sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    subframes_per_step = len(L_SWEEP) * N_SF
+    subframes_per_step = nfr * N_SF
     value = world * subframes_per_step * args.steps / (total_ms / 1e3)
+    nmse = np.array([float(f["err"][2].item()) for f in fr])
 
-    # per-kernel durations from the library's event timing over the timed steps
+    # the same step one frame at a time on one stream: the kernels run alone, so their
+    # per-launch CUDA-event durations are the kernels' own (roofline of the dominant one)
+    for _ in range(args.warmup):
+        step_sequential()
+    barrier()
+    seq_ms = timed_steps(step_sequential, args.steps, profile=True)
+    seq_total = float(sum(seq_ms))
+    seq_value = world * subframes_per_step * args.steps / (seq_total / 1e3)
     fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "err_pass1",
-            "err_pass2", "err_finish"]
+            "err_pass2"]
     prof = {f: holo.holo_profile_read(f) for f in fams}
     npairs = (N_SF + 1) // 2
     chunk = min(npairs, tuning["chunk"])
@@ -325,6 +354,7 @@ def run_ours(args):
                 "frac": achieved / peak_bw if achieved else None, "traffic": traffic,
                 "traffic_source": traffic_src,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "timed_in": "sequential leg (one frame at a time, CUDA events around every launch)",
                 "algorithmic_bytes_per_launch": bytes_dom,
                 "avg_launch_us": ms_dom / n_dom * 1e3 if n_dom else None,
                 "kernel_share": {f: round(prof[f][1] / max(1e-12, sum(v[1] for v in prof.values())), 4)
@@ -334,7 +364,7 @@ def run_ours(args):
 
     # GS leg: 1024^2, 20 iterations, LUT-random start
     gcodes = torch.empty(GS_L, dtype=torch.uint8, device=dev)
-    holo.lut_build(LUT_SEED, GS_L, 256, gcodes, None, stream=stream.cuda_stream)
+    holo.lut_build(LUT_SEED, GS_L, 256, gcodes, None, stream=s)
     gws = torch.empty(holo.gs_workspace_size(H, W, GS_ITERS), dtype=torch.uint8, device=dev)
     gq = torch.empty((H, W), dtype=torch.uint8, device=dev)
     gI = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -363,36 +393,29 @@ def run_ours(args):
     gs_nmse = float(gout[2].item())
     gs_ips = GS_ITERS * gs_runs / (gs_ms / 1e3)
 
-    # end to end through the public API: host target in, bits + replay + error out
+    # end to end through the public API: every frame's target copied in from pinned host
+    # memory, the batch call, bits + replay + error of every frame copied back
     h_targets = [t.cpu().pin_memory() for t in targets]
-    h_bits = torch.empty((N_SF, P // 32), dtype=torch.int32).pin_memory()
-    h_replay = torch.empty((H, W), dtype=torch.float32).pin_memory()
-    h_err = torch.empty(3, dtype=torch.float64).pin_memory()
-    d_tgt = torch.empty((H, W), dtype=torch.float32, device=dev)
+    h_out = [{"bits": torch.empty((N_SF, P // 32), dtype=torch.int32).pin_memory(),
+              "I": torch.empty((H, W), dtype=torch.float32).pin_memory(),
+              "err": torch.empty(3, dtype=torch.float64).pin_memory()} for _ in fr]
     e2e_steps = max(1, min(args.steps, 10))
 
     def e2e_step():
-        for i, L in enumerate(L_SWEEP):
-            d_tgt.copy_(h_targets[i % 2], non_blocking=True)
-            frame(i, L, d_tgt)
-            h_bits.copy_(bits, non_blocking=True)
-            h_replay.copy_(replay, non_blocking=True)
-            h_err.copy_(errs[i], non_blocking=True)
+        for i, f in enumerate(fr):
+            f["T"].copy_(h_targets[i % 2], non_blocking=True)
+        step_batch()
+        for f, h in zip(fr, h_out):
+            h["bits"].copy_(f["bits"], non_blocking=True)
+            h["I"].copy_(f["I"], non_blocking=True)
+            h["err"].copy_(f["err"], non_blocking=True)
 
     e2e_step()
     barrier()
-    e2e_ms = 0.0
-    for _ in range(e2e_steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e2e_step()
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = float(sum(timed_steps(e2e_step, e2e_steps)))
     e2e_value = world * subframes_per_step * e2e_steps / (e2e_ms / 1e3)
-    nmse = errs[:, 2].cpu().numpy()
+    e2e_nmse = np.array([float(h["err"][2]) for h in h_out])
+    assert np.allclose(e2e_nmse, nmse, rtol=0, atol=0), "end-to-end outputs differ from the device-resident run"
 
     batch = run_batch_leg(dev, stream) if not args.no_batch else None
     precision_leg = run_precision_leg(dev, stream) if not args.no_batch else None
@@ -411,9 +434,12 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "tuning": dict(tuning, autotune_ms_per_frame=tune_ms),
             "config": {"workload": "ospr_1024x1024_N24_Lsweep", "H": H, "W": W, "N": N_SF,
-                       "L": "2^8..2^20 + unrepeated", "frames_per_step": len(L_SWEEP),
+                       "L": "2^8..2^20 + unrepeated", "frames_per_step": nfr,
+                       "step": "one ospr_generate_batch call: per frame lut_build + ospr_generate + replay_error",
                        "targets": "seeded blob / band-limited noise", "l2": "flushed before each step",
                        "parallelism": f"replicas x{world}"},
+            "sequential": {"value": seq_value, "unit": "sub-frames/s", "ms_per_step": seq_total / args.steps,
+                           "how": "the same step one frame at a time on one stream (per-frame API calls)"},
             "roofline": roofline,
             "path_bytes_model": {"bytes_per_subframe": sf_bytes, "achieved_GBps": path_gbs,
                                  "frac_of_hbm": path_gbs / peak_bw},

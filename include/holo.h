@@ -77,7 +77,7 @@ int holo_launch_count(uint64_t* out_count);
  * milliseconds since the last holo_profile_reset. Families: "lut_build",
  * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "gs_prepare",
  * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2",
- * "err_finish", "nn_conv_fwd", "nn_conv_dgrad", "nn_conv_wgrad", "nn_elementwise",
+ * "nn_conv_fwd", "nn_conv_dgrad", "nn_conv_wgrad", "nn_elementwise",
  * "nn_loss", "nn_adam". */
 int holo_profile_enable(int on);
 int holo_profile_reset(void);
@@ -152,23 +152,29 @@ int ospr_generate(const float* d_target, int H, int W, int N,
                   void* d_ws, size_t ws_bytes, holo_stream_t s);
 
 /*
- * OSPR tuning per shape (H, W): the tile variant of the column passes and of the row pass
- * (0 or 1; lengths below 512 have only variant 0), the sub-frame pairs in flight per
- * chunk (1..16) and the partial accumulators of the column DFT pass (1..4). Every
- * setting computes the same values up to float32 rounding order; the workspace size of
- * ospr_workspace_size follows the current setting, so query it after changing it.
+ * OSPR tuning per shape (H, W): the tile variants of the column IDFT pass and of the
+ * column DFT pass (0..2 each: radix-32 lines at two widths, radix-16 lines; lengths below
+ * 512 have only variant 0), of the row pass (0..1; only 0 below 512), the sub-frame pairs
+ * in flight per chunk (1..16) and the partial accumulators of the column DFT pass (1..4).
+ * A variant a length does not have falls back to 0. Every setting computes the same
+ * values up to float32 rounding order; the workspace size of ospr_workspace_size follows
+ * the current setting, so query it after changing it.
  * ospr_autotune times ospr_generate on synthetic data of this shape (a 10007-entry table)
- * for candidate settings (coordinate descent: column variant, row variant, chunk, groups;
- * each the median of `reps` runs after one warm-up, CUDA events on stream s), installs the
- * fastest for this process and, when the environment variable HOLO_TUNE_CACHE names a
- * file, writes every installed setting there (one JSON object per line), from where later
- * processes read it. It allocates and frees its own scratch (HOLO_ENOMEM if that fails)
- * and synchronises s. best_ms (nullable) receives the winner's time per call.
- * ospr_tuning_set installs a setting without timing (for tests and reproduction).
+ * for candidate settings (two sweeps of coordinate descent over the column IDFT variant,
+ * row variant, column DFT variant, chunk and groups; each candidate the median of `reps`
+ * runs after one warm-up, CUDA events on stream s), installs the fastest for this process
+ * and, when the environment variable HOLO_TUNE_CACHE names a file, writes every installed
+ * setting there (one JSON object per line), from where later processes read it. It
+ * allocates and frees its own scratch (HOLO_ENOMEM if that fails) and synchronises s.
+ * best_ms (nullable) receives the winner's time per call.
+ * ospr_tuning_set installs a setting without timing (for tests and reproduction); values
+ * outside the ranges above are HOLO_EINVAL.
  */
 int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, double* best_ms);
-int ospr_tuning_get(int H, int W, int* col_variant, int* row_variant, int* chunk, int* groups);
-int ospr_tuning_set(int H, int W, int col_variant, int row_variant, int chunk, int groups);
+int ospr_tuning_get(int H, int W, int* col_ifft_variant, int* col_fft_variant, int* row_variant, int* chunk,
+                    int* groups);
+int ospr_tuning_set(int H, int W, int col_ifft_variant, int col_fft_variant, int row_variant, int chunk,
+                    int groups);
 
 /*
  * ospr_generate_noalloc - ospr_generate for callers that cannot allocate device memory.
@@ -379,7 +385,11 @@ int replay_error_workspace_size(int H, int W, size_t* bytes);
  * with the intensity-domain, optimal-scale reading:
  *   alpha = sum(I*T^2) / sum(I^2);  mse = sum((alpha*I - T^2)^2) / P;
  *   nmse  = sum((alpha*I - T^2)^2) / sum(T^4)
- * All sums in float64, two passes, fixed reduction order (bit-reproducible).
+ * Each thread sums a few pixels' terms in float32 (single-rounding fmaf); sums across
+ * threads and blocks are float-float (about 48 significant bits) in a fixed order, so
+ * results are bit-reproducible; only the three outputs are float64. Two launches (the
+ * second one's last block to finish writes mse and nmse); the workspace holds the block
+ * partial sums and a completion counter the first launch clears.
  *
  *   d_replay  [H][W] float32 intensity I.   d_target [H][W] float32 amplitude T.
  *   d_mask    [H][W] uint8 or NULL: nonzero pixels are included (P = their count).

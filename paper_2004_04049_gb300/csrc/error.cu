@@ -2,11 +2,12 @@
 // optimal-scale reading: alpha = sum(I T^2)/sum(I^2), mse = sum((alpha I - T^2)^2)/P,
 // nmse = sum((alpha I - T^2)^2)/sum(T^4).
 //
-// Three launches, no atomics:
+// Two launches:
 //   partials1  per block: sum I*T^2, sum I^2, sum T^4, count
 //   partials2  every block first reduces partials1 to alpha (one warp, fixed order, so
-//              every block gets the same bits), then its share of sum (alpha I - T^2)^2
-//   finish     one warp: mse and nmse from partials2
+//              every block gets the same bits), then its share of sum (alpha I - T^2)^2;
+//              the block that finishes last (a completion counter, no waiting) adds the
+//              shares in block order and writes mse and nmse
 // Each thread forms its terms with single-rounding fmaf in float32 over a few pixels;
 // every sum across threads, warps and blocks is float-float (about 48 significant bits,
 // ffloat.cuh) in a fixed order, so results are bit-reproducible, and only the three
@@ -54,11 +55,13 @@ __device__ __forceinline__ float4 mask4(const uint8_t* __restrict__ m, int64_t q
     return make_float4(b.x ? 1.f : 0.f, b.y ? 1.f : 0.f, b.z ? 1.f : 0.f, b.w ? 1.f : 0.f);
 }
 
-// partials laid out [k][nb]: k = 0 sum I T^2, 1 sum I^2, 2 sum T^4, 3 count
+// partials laid out [k][nb]: k = 0 sum I T^2, 1 sum I^2, 2 sum T^4, 3 count. Block 0 also
+// clears the completion counter of pass 2 (which runs after this launch on the stream).
 __global__ void __launch_bounds__(kErrThreads)
 k_err_pass1(const float* __restrict__ I, const float* __restrict__ T, const uint8_t* __restrict__ mask,
-            int64_t P, ff* __restrict__ partials) {
+            int64_t P, ff* __restrict__ partials, unsigned* __restrict__ done) {
     __shared__ ff sm[32 * 4];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0u;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
@@ -102,10 +105,11 @@ k_err_pass1(const float* __restrict__ I, const float* __restrict__ T, const uint
 
 __global__ void __launch_bounds__(kErrThreads)
 k_err_pass2(const float* __restrict__ I, const float* __restrict__ T, const uint8_t* __restrict__ mask,
-            int64_t P, const ff* __restrict__ partials1, ff* __restrict__ partials2,
+            int64_t P, const ff* __restrict__ partials1, ff* partials2, unsigned* done,
             double* __restrict__ d_out) {
     __shared__ ff sm[32];
     __shared__ float s_alpha;
+    __shared__ bool s_last;
     const int nb = gridDim.x;
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
@@ -148,24 +152,30 @@ k_err_pass2(const float* __restrict__ I, const float* __restrict__ T, const uint
     }
     ff b[1];
     block_sums_ff<1>(acc, b, sm);
-    if (threadIdx.x == 0) partials2[blockIdx.x] = b[0];
-}
-
-__global__ void __launch_bounds__(32)
-k_err_finish(const ff* __restrict__ partials1, const ff* __restrict__ partials2, int nb,
-             double* __restrict__ d_out) {
+    // publish this block's share; the block whose increment completes the count reduces
+    // all shares (threadfence reduction: every other block fenced its store before its
+    // increment, and the last block reads the shares through L2)
+    if (threadIdx.x == 0) {
+        partials2[blockIdx.x] = b[0];
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == unsigned(nb - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32) return;
+    __threadfence();
     const ff s_tt = warp_sum_array_ff(partials1 + 2 * nb, nb);
     const ff count = warp_sum_array_ff(partials1 + 3 * nb, nb);
-    const ff sse = warp_sum_array_ff(partials2, nb);
+    const ff sse = warp_sum_array_ff_cg(partials2, nb);
     if (threadIdx.x == 0) {
         d_out[1] = count.hi > 0.f ? ff_to_double(ff_div(sse, count)) : 0.0;
         d_out[2] = s_tt.hi > 0.f ? ff_to_double(ff_div(sse, s_tt)) : 0.0;
     }
 }
 
+static size_t err_part_bytes(int nb) { return align_up(sizeof(ff) * size_t(nb) * 4, 256); }
 static size_t err_ws_bytes(int64_t P) {
     const int nb = err_blocks(P);
-    return align_up(sizeof(ff) * size_t(nb) * 4, 256) + align_up(sizeof(ff) * size_t(nb), 256);
+    return err_part_bytes(nb) + align_up(sizeof(ff) * size_t(nb), 256) + 256;
 }
 
 }  // namespace holo
@@ -196,19 +206,16 @@ extern "C" int replay_error(const float* d_replay, const float* d_target, const 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
     const int nb = err_blocks(P);
     ff* part1 = static_cast<ff*>(d_ws);
-    ff* part2 = part1 + align_up(sizeof(ff) * size_t(nb) * 4, 256) / sizeof(ff);
+    ff* part2 = part1 + err_part_bytes(nb) / sizeof(ff);
+    unsigned* done = reinterpret_cast<unsigned*>(static_cast<char*>(d_ws) + err_part_bytes(nb) +
+                                                 align_up(sizeof(ff) * size_t(nb), 256));
     int rc;
     {
         Launch ln("err_pass1", st);
-        k_err_pass1<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1);
+        k_err_pass1<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1, done);
         if ((rc = ln.done("err_pass1 launch"))) return rc;
     }
-    {
-        Launch ln("err_pass2", st);
-        k_err_pass2<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1, part2, d_out);
-        if ((rc = ln.done("err_pass2 launch"))) return rc;
-    }
-    Launch ln("err_finish", st);
-    k_err_finish<<<1, 32, 0, st>>>(part1, part2, nb, d_out);
-    return ln.done("err_finish launch");
+    Launch ln("err_pass2", st);
+    k_err_pass2<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1, part2, done, d_out);
+    return ln.done("err_pass2 launch");
 }
