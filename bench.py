@@ -431,6 +431,7 @@ def run_ours(args):
             "metric": "OSPR 1024x1024 binary sub-frames/s (L sweep 2^8..2^20 + unrepeated, N=24)",
             "value": value, "unit": "sub-frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "step_ms_p10_p50_p90": [float(np.percentile(step_ms, q)) for q in (10, 50, 90)],
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "tuning": dict(tuning, autotune_ms_per_frame=tune_ms),
             "config": {"workload": "ospr_1024x1024_N24_Lsweep", "H": H, "W": W, "N": N_SF,
@@ -595,9 +596,9 @@ def run_precision_leg(dev, stream, reps=5):
 
 
 # ------------------------------------------------------------- CPU oracle arm ----
-def _oracle_subframes(n_sub, L=1 << 16):
-    """Runs n_sub sub-frames of the workload's 1024x1024 frame through the oracle."""
-    from oracle import error as oerr
+def _oracle_partial(s0, n_sub, L=1 << 16):
+    """Sub-frames s0 .. s0+n_sub-1 of the workload's 1024x1024 frame through the oracle:
+    their bits and summed replay intensity."""
     from oracle import lut as olut
     from oracle import ospr as oospr
     from synthetic import blob_target
@@ -606,17 +607,33 @@ def _oracle_subframes(n_sub, L=1 << 16):
     table = olut.lut_codes(LUT_SEED, L)
     P = H * W
     I = np.zeros((H, W))
-    for s in range(n_sub):
+    for s in range(s0, s0 + n_sub):
         c = olut.subframe_codes(table, L, LUT_SEED, 0, s, P, P)
         Hs = oospr.back_propagate(oospr.subframe_field(T, c))
         h = oospr.binarise(Hs.real)
         oospr.pack_bits(h)
         I += oospr.replay_intensity(h)
-    oerr.replay_error(I / n_sub, T)
+    return I
+
+
+def _oracle_subframes(n_sub, L=1 << 16):
+    """Runs n_sub sub-frames of the workload's 1024x1024 frame through the oracle."""
+    from oracle import error as oerr
+    from synthetic import blob_target
+
+    I = _oracle_partial(0, n_sub, L)
+    oerr.replay_error(I / n_sub, blob_target(H, W, 1000))
+
+
+def _oracle_worker(job):
+    return _oracle_partial(*job)
 
 
 def cpu_baseline_sample(seconds=15.0):
-    """The oracle as it stands on the host cores: sub-frames of the 1024x1024 workload."""
+    """The oracle as it stands on the host cores: sub-frames of the 1024x1024 workload, on
+    one core and then on every core (one process per core, spawned)."""
+    import multiprocessing as mp
+
     t0 = time.perf_counter()
     _oracle_subframes(1)
     one = time.perf_counter() - t0
@@ -624,9 +641,23 @@ def cpu_baseline_sample(seconds=15.0):
     t0 = time.perf_counter()
     _oracle_subframes(n)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "sub-frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} sub-frames of the 1024x1024 L=65536 frame (float64 numpy oracle, "
-                      f"one thread), {dt:.1f} s"}
+    single = {"value": n / dt, "cores": 1,
+              "sample": f"{n} sub-frames of the 1024x1024 L=65536 frame (float64 numpy oracle, one process), "
+                        f"{dt:.1f} s"}
+    cores = os.cpu_count() or 1
+    per = max(1, int(seconds / max(one, 1e-3)))
+    jobs = [(k * per, per) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_worker, [(0, 1)] * cores)      # imports and table set-up in every worker
+        t0 = time.perf_counter()
+        parts = pool.map(_oracle_worker, jobs)
+        dtp = time.perf_counter() - t0
+    del parts
+    nall = per * cores
+    return {"value": nall / dtp, "unit": "sub-frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nall} sub-frames of the 1024x1024 L=65536 frame, {per} per process on {cores} spawned "
+                      f"processes (float64 numpy oracle), {dtp:.1f} s",
+            "single_core": single}
 
 
 def run_reference(args):
@@ -656,6 +687,51 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# (name, B, R, Cin, Cout): the warm-start network's layer shapes at the training batch
+CONV_SHAPES = [("enc0_8to32_256sq", 16, 256, 8, 32), ("enc1_32to32_256sq", 16, 256, 32, 32),
+               ("enc3_64to64_128sq", 16, 128, 64, 64), ("enc5_128to128_64sq", 16, 64, 128, 128),
+               ("mid_128to128_32sq", 16, 32, 128, 128), ("dec9_128to64_128sq", 16, 128, 128, 64),
+               ("dec10_64to32_256sq", 16, 256, 64, 32)]
+
+
+def conv_throughput(reps=20):
+    """Forward 3x3 convolution of every network layer shape: the tcgen05 kernel against the
+    mma.sync kernel (TFLOP/s = 2*B*R^2*Cin*Cout*9 per call / CUDA-event time)."""
+    import torch
+
+    from paper_2004_04049_gb300 import holo
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, B, R, Ci, Co in CONV_SHAPES:
+        x = torch.randn((B, R, R, Ci), device=dev).to(torch.bfloat16)
+        w = (0.05 * torch.randn((Co, 9 * Ci), device=dev)).to(torch.bfloat16)
+        bias = torch.zeros(Co, dtype=torch.float32, device=dev)
+        y = torch.empty((B, R, R, Co), dtype=torch.bfloat16, device=dev)
+        flops = 2.0 * B * R * R * Ci * Co * 9
+        row = {}
+        for kind, mode in (("tcgen05", 0), ("mma_sync", holo.HOLO_CONV_LEGACY)):
+            def call():
+                holo.nn_conv3x3(mode, B, R, R, Ci, Co, x, w, d_bias=bias, d_out=y, relu=True,
+                                stream=stream.cuda_stream)
+
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                call()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[kind] = {"us": ms * 1e3, "tflops": flops / (ms / 1e3) / 1e12}
+        out[name] = row
+    out["tc_fault"] = holo.nn_tc_status()
+    return out
+
+
 def run_learned(args):
     """Learned GS warm start at the configured scale (labels from 100-iteration GS on 20k
     seeded 256^2 targets, training by the library's kernels, evaluation at 1024^2), plus
@@ -666,29 +742,7 @@ def run_learned(args):
 
     build_lib.build()
     holo.load()
-    dev = torch.device("cuda:0")
-    stream = torch.cuda.current_stream(dev)
-    conv = {}
-    for name, (B, R, C) in {"c1b_32ch_256sq": (16, 256, 32), "c3b_128ch_64sq": (16, 64, 128)}.items():
-        x = torch.randn((B, R, R, C), device=dev).to(torch.bfloat16)
-        w = (0.05 * torch.randn((C, 9 * C), device=dev)).to(torch.bfloat16)
-        y = torch.empty((B, R, R, C), dtype=torch.bfloat16, device=dev)
-        flops = 2.0 * B * R * R * C * C * 9
-
-        def call():
-            holo.nn_conv3x3(0, B, R, R, C, C, x, w, d_out=y, relu=True, stream=stream.cuda_stream)
-
-        for _ in range(3):
-            call()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(20):
-            call()
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / 20
-        conv[name] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
+    conv = conv_throughput()
     res = warmstart.run(n_train=args.learned_n, gs_iters=100, epochs=args.learned_epochs, batch=16,
                         eval_size=1024, n_eval=8, log=lambda s: print(s, file=sys.stderr))
     peaks = _peaks()
@@ -741,6 +795,7 @@ def main():
     ap.add_argument("--learned", action="store_true", help="run the learned GS warm-start experiment")
     ap.add_argument("--learned-n", type=int, default=20000)
     ap.add_argument("--learned-epochs", type=int, default=2)
+    ap.add_argument("--conv", action="store_true", help="time the network's convolution kernels only")
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="store per-launch DRAM bytes from an ncu --csv log in profiles/dram_traffic.json")
     ap.add_argument("--traffic-command", default="", help="the ncu command that wrote the CSV")
@@ -751,6 +806,14 @@ def main():
         return
     if args.learned:
         run_learned(args)
+        return
+    if args.conv:
+        from paper_2004_04049_gb300 import build_lib, holo
+        build_lib.build()
+        holo.load()
+        peaks = _peaks()
+        print(json.dumps({"conv_kernel": conv_throughput(),
+                          "bf16_peak_tflops": peaks["bf16_tflops"] if peaks else 1900.0}), flush=True)
         return
     if args.case:
         from paper_2004_04049_gb300 import build_lib

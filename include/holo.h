@@ -306,6 +306,17 @@ int gs_iterate(const float* d_target, int H, int W, int iters, int levels,
                const float* d_state_in, float* d_state_out,
                void* d_ws, size_t ws_bytes, holo_stream_t s);
 
+/*
+ * GS tile variants per shape (an engineering choice, not part of the method): the column
+ * passes and the row pass each have variants 0..2 for line lengths 512..2048 (variant 0
+ * only for other lengths; other values fall back to 0). Every variant computes the same
+ * values up to float32 rounding order. Defaults are the fastest measured on GB300
+ * (1024: column 0, row 1; 2048: column 1, row 1). gs_tuning_set with a negative variant
+ * restores the defaults of the shape. Host-only calls; HOLO_EINVAL outside -1..2.
+ */
+int gs_tuning_set(int H, int W, int col_variant, int row_variant);
+int gs_tuning_get(int H, int W, int* col_variant, int* row_variant);
+
 /* ------------------------------------------------------- learned warm start ---- */
 
 /*
@@ -360,7 +371,11 @@ int ws_load(ws_net* net, const char* path);
 
 /*
  * nn_conv3x3 - the network's convolution kernel on its own (3x3, zero padding 1, stride
- * 1, channels-last bf16 tensors, channels multiples of 8, float32 accumulation):
+ * 1, channels-last bf16 tensors, channels multiples of 8, float32 accumulation). Modes 0
+ * and 1 run on the tcgen05 tensor cores (accumulator in tensor memory) when the output
+ * width is 32, 64 or 128 and every tensor is 16-byte aligned, else on the mma.sync kernel;
+ * mode | HOLO_CONV_LEGACY forces the mma.sync kernel (for comparisons). Mode 2 always
+ * uses the mma.sync kernel.
  *   mode 0 forward: d_out[p][o] = act(sum X(p,k) W[o][k] + bias[o] + residual[p][o]) with
  *          d_in [B][H][W][Cin], d_wmat [Cout][9*Cin] bf16, bias/residual nullable,
  *          outputs bf16 d_out and/or float32 d_out_f32;
@@ -369,9 +384,18 @@ int ws_load(ws_net* net, const char* path);
  *   mode 2 weight gradient: d_dw [Cout][9*Cin] float32 += sum_p d_dy[p][o] X(p, k) with
  *          d_in = x [B][H][W][Cin], d_dy [B][H][W][Cout].
  */
+#define HOLO_CONV_LEGACY 16
 int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, const void* d_in, const void* d_wmat,
                const void* d_dy, const float* d_bias, const void* d_residual, int relu, void* d_out,
                float* d_out_f32, float* d_dw, holo_stream_t s);
+
+/*
+ * nn_tc_status - the tcgen05 convolution kernels bound every wait on their pipeline
+ * barriers; a wait that expires makes the kernel skip its outputs, free its tensor memory
+ * and set a device flag. Writes that flag to *fault (0 = never) and clears it when
+ * `clear` is nonzero. Synchronous (reads device memory).
+ */
+int nn_tc_status(int* fault, int clear);
 
 /* ------------------------------------------------------------ replay error ---- */
 

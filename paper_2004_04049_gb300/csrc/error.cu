@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kErrThreads)
 k_err_pass1(const float* __restrict__ I, const float* __restrict__ T, const uint8_t* __restrict__ mask,
             int64_t P, ff* __restrict__ partials, unsigned* __restrict__ done) {
     __shared__ ff sm[32 * 4];
+    pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0u;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -110,6 +111,7 @@ k_err_pass2(const float* __restrict__ I, const float* __restrict__ T, const uint
     __shared__ ff sm[32];
     __shared__ float s_alpha;
     __shared__ bool s_last;
+    pdl_wait();
     const int nb = gridDim.x;
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
@@ -212,10 +214,12 @@ extern "C" int replay_error(const float* d_replay, const float* d_target, const 
     int rc;
     {
         Launch ln("err_pass1", st);
-        k_err_pass1<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1, done);
-        if ((rc = ln.done("err_pass1 launch"))) return rc;
+        const cudaError_t le = launch_pdl(k_err_pass1, dim3(nb), dim3(kErrThreads), 0, st, d_replay, d_target,
+                                          d_mask, P, part1, done);
+        if ((rc = ln.done("err_pass1 launch", le))) return rc;
     }
     Launch ln("err_pass2", st);
-    k_err_pass2<<<nb, kErrThreads, 0, st>>>(d_replay, d_target, d_mask, P, part1, part2, done, d_out);
-    return ln.done("err_pass2 launch");
+    const cudaError_t le = launch_pdl(k_err_pass2, dim3(nb), dim3(kErrThreads), 0, st, d_replay, d_target, d_mask,
+                                      P, static_cast<const ff*>(part1), part2, done, d_out);
+    return ln.done("err_pass2 launch", le);
 }

@@ -14,6 +14,9 @@
 //              |R|^2 and the state instead of transforming back
 //   finish     per-iteration float64 error sums
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "ffloat.cuh"
 #include "fft_core.cuh"
@@ -22,23 +25,39 @@
 
 namespace holo {
 
-// column passes: small column tiles so that a single field fills the GPU
-template <int N> struct GsColCfg;
-template <> struct GsColCfg<64>   { static constexpr int R = 8,  LPC = 8; };
-template <> struct GsColCfg<128>  { static constexpr int R = 16, LPC = 8; };
-template <> struct GsColCfg<256>  { static constexpr int R = 16, LPC = 8; };
-template <> struct GsColCfg<512>  { static constexpr int R = 16, LPC = 4; };
-template <> struct GsColCfg<1024> { static constexpr int R = 16, LPC = 4; };
-template <> struct GsColCfg<2048> { static constexpr int R = 32, LPC = 4; };
-template <> struct GsColCfg<4096> { static constexpr int R = 32, LPC = 2; };
-template <int N> struct GsRowCfg;
-template <> struct GsRowCfg<64>   { static constexpr int R = 2,  LPR = 4; };
-template <> struct GsRowCfg<128>  { static constexpr int R = 4,  LPR = 4; };
-template <> struct GsRowCfg<256>  { static constexpr int R = 8,  LPR = 4; };
-template <> struct GsRowCfg<512>  { static constexpr int R = 16, LPR = 4; };
-template <> struct GsRowCfg<1024> { static constexpr int R = 32, LPR = 4; };
-template <> struct GsRowCfg<2048> { static constexpr int R = 32, LPR = 2; };
-template <> struct GsRowCfg<4096> { static constexpr int R = 32, LPR = 1; };
+// column passes: small column tiles so that a single field fills the GPU. Lengths 512 to
+// 2048 have two more tile variants (fewer values per thread, or fewer lines per CTA),
+// chosen per shape with gs_tuning_set; the defaults are the fastest measured on GB300.
+template <int N, int V> struct GsColCfg;
+template <> struct GsColCfg<64, 0>   { static constexpr int R = 8,  LPC = 8; };
+template <> struct GsColCfg<128, 0>  { static constexpr int R = 16, LPC = 8; };
+template <> struct GsColCfg<256, 0>  { static constexpr int R = 16, LPC = 8; };
+template <> struct GsColCfg<512, 0>  { static constexpr int R = 16, LPC = 4; };
+template <> struct GsColCfg<1024, 0> { static constexpr int R = 16, LPC = 4; };
+template <> struct GsColCfg<2048, 0> { static constexpr int R = 32, LPC = 4; };
+template <> struct GsColCfg<4096, 0> { static constexpr int R = 32, LPC = 2; };
+template <> struct GsColCfg<512, 1>  { static constexpr int R = 8,  LPC = 4; };
+template <> struct GsColCfg<1024, 1> { static constexpr int R = 8,  LPC = 4; };
+template <> struct GsColCfg<2048, 1> { static constexpr int R = 16, LPC = 4; };
+template <> struct GsColCfg<512, 2>  { static constexpr int R = 16, LPC = 2; };
+template <> struct GsColCfg<1024, 2> { static constexpr int R = 16, LPC = 2; };
+template <> struct GsColCfg<2048, 2> { static constexpr int R = 32, LPC = 2; };
+template <int N, int V> struct GsRowCfg;
+template <> struct GsRowCfg<64, 0>   { static constexpr int R = 2,  LPR = 4; };
+template <> struct GsRowCfg<128, 0>  { static constexpr int R = 4,  LPR = 4; };
+template <> struct GsRowCfg<256, 0>  { static constexpr int R = 8,  LPR = 4; };
+template <> struct GsRowCfg<512, 0>  { static constexpr int R = 16, LPR = 4; };
+template <> struct GsRowCfg<1024, 0> { static constexpr int R = 32, LPR = 4; };
+template <> struct GsRowCfg<2048, 0> { static constexpr int R = 32, LPR = 2; };
+template <> struct GsRowCfg<4096, 0> { static constexpr int R = 32, LPR = 1; };
+template <> struct GsRowCfg<512, 1>  { static constexpr int R = 8,  LPR = 4; };
+template <> struct GsRowCfg<1024, 1> { static constexpr int R = 16, LPR = 2; };
+template <> struct GsRowCfg<2048, 1> { static constexpr int R = 16, LPR = 1; };
+template <> struct GsRowCfg<512, 2>  { static constexpr int R = 16, LPR = 2; };
+template <> struct GsRowCfg<1024, 2> { static constexpr int R = 8,  LPR = 2; };
+template <> struct GsRowCfg<2048, 2> { static constexpr int R = 16, LPR = 2; };
+constexpr bool gs_has_variants(int N) { return N >= 512 && N <= 2048; }
+constexpr int kGsMinLpc = 2;   // the smallest LPC of any variant (bounds the error partials)
 
 constexpr int kGsPrepThreads = 256;
 constexpr int kGsPrepBlocks = 152;
@@ -67,16 +86,16 @@ struct GsArgs {
     float inv_sqrt_p;
 };
 
-template <int NC>
-constexpr int gs_col_stride() { return col_line_stride(NC, GsColCfg<NC>::R, GsColCfg<NC>::LPC); }
+template <int NC, int V>
+constexpr int gs_col_stride() { return col_line_stride(NC, GsColCfg<NC, V>::R, GsColCfg<NC, V>::LPC); }
 // col_init and row also hold one copy of the cos/sin table (one lookup per pixel)
-template <int NC>
+template <int NC, int V>
 constexpr size_t gs_col_smem() {
-    return sizeof(float2) * (256 + size_t(GsColCfg<NC>::LPC) * gs_col_stride<NC>());
+    return sizeof(float2) * (256 + size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>());
 }
-template <int NR>
+template <int NR, int V>
 constexpr size_t gs_row_smem() {
-    return sizeof(float2) * (256 + size_t(GsRowCfg<NR>::LPR) * line_stride(NR, GsRowCfg<NR>::R));
+    return sizeof(float2) * (256 + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
 }
 
 // ----------------------------------------------------------------- prepare ----
@@ -99,14 +118,15 @@ __device__ __forceinline__ float gs_scale(const ff* __restrict__ partials, int64
 }
 
 // --------------------------------------------------------------- col_init ----
-template <int NC>
-__global__ void __launch_bounds__((NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC)
+template <int NC, int V>
+__global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC)
 k_gs_col_init(GsArgs a) {
-    constexpr int R = GsColCfg<NC>::R, LPC = GsColCfg<NC>::LPC, T = NC / R;
+    constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
     extern __shared__ float2 sm[];
     float2* cs = sm;
     float2* lines = sm + 256;
     load_cs_table<1>(cs, a.cs256);
+    pdl_wait();
     __syncthreads();
     __shared__ float s_scale;
     if (threadIdx.x < 32) {
@@ -136,24 +156,26 @@ k_gs_col_init(GsArgs a) {
             v[e] = make_float2(ts * ph.x, ts * ph.y);
         }
     }
-    line_fft<NC, R, +1, true>(v, lines + lc * gs_col_stride<NC>(), t, a.tw);
+    line_fft<NC, R, +1, true>(v, lines + lc * gs_col_stride<NC, V>(), t, a.tw);
+    pdl_trigger();
 #pragma unroll
     for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
 }
 
 // -------------------------------------------------------------------- row ----
-template <int NR>
-__global__ void __launch_bounds__((NR / GsRowCfg<NR>::R) * GsRowCfg<NR>::LPR)
+template <int NR, int V>
+__global__ void __launch_bounds__((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR)
 k_gs_row(GsArgs a) {
-    constexpr int R = GsRowCfg<NR>::R, T = NR / R;
+    constexpr int R = GsRowCfg<NR, V>::R, T = NR / R;
     constexpr bool BLOCK = T > 32;
     extern __shared__ float2 sm[];
     float2* cs = sm;
     float2* lines = sm + 256;
     load_cs_table<1>(cs, a.cs256);
+    pdl_wait();
     __syncthreads();
     const int line = threadIdx.x / T, t = threadIdx.x % T;
-    const int r = blockIdx.x * GsRowCfg<NR>::LPR + line;
+    const int r = blockIdx.x * GsRowCfg<NR, V>::LPR + line;
     float2* z = a.y + size_t(r) * NR;
     float2* buf = lines + line * line_stride(NR, R);
     float2 v[R];
@@ -171,22 +193,24 @@ k_gs_row(GsArgs a) {
         v[e] = cs_lookup<1>(cs, uint32_t(q) << shift);
     }
     line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
+    pdl_trigger();
 #pragma unroll
     for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
 }
 
 // -------------------------------------------------------------------- col ----
-template <int NC, bool LAST>
-__global__ void __launch_bounds__((NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC)
+template <int NC, int V, bool LAST>
+__global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC)
 k_gs_col(GsArgs a) {
-    constexpr int R = GsColCfg<NC>::R, LPC = GsColCfg<NC>::LPC, T = NC / R;
+    constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
     extern __shared__ float2 sm[];
     __shared__ ff red[32];
     float2* lines = sm;
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
-    float2* buf = lines + lc * gs_col_stride<NC>();
+    float2* buf = lines + lc * gs_col_stride<NC, V>();
+    pdl_wait();
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = a.y[size_t(t + T * e) * W + c];
@@ -218,6 +242,7 @@ k_gs_col(GsArgs a) {
     if (threadIdx.x == 0) a.err_part[size_t(a.iter) * gridDim.x + blockIdx.x] = b[0];
     if constexpr (!LAST) {
         line_fft<NC, R, +1, true>(v, buf, t, a.tw);
+        pdl_trigger();
 #pragma unroll
         for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
     }
@@ -226,82 +251,102 @@ k_gs_col(GsArgs a) {
 // ----------------------------------------------------------------- finish ----
 __global__ void __launch_bounds__(32)
 k_gs_finish(const ff* __restrict__ err_part, int nb, double* __restrict__ err) {
+    pdl_wait();
     const ff v = warp_sum_array_ff(err_part + size_t(blockIdx.x) * nb, nb);
     if (threadIdx.x == 0) err[blockIdx.x] = ff_to_double(v);
 }
 
 // ------------------------------------------------------------------- host ----
-template <int NC>
-static int launch_col_init(const GsArgs& a, cudaStream_t st) {
-    static uint64_t mask = 0;
-    constexpr size_t smem = gs_col_smem<NC>();
-    int rc = ensure_smem((const void*)k_gs_col_init<NC>, smem, &mask);
-    if (rc) return rc;
-    Launch ln("gs_col_init", st);
-    k_gs_col_init<NC><<<a.W / GsColCfg<NC>::LPC, (NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC, smem, st>>>(a);
-    return ln.done("gs_col_init launch");
-}
-template <int NR>
-static int launch_row(const GsArgs& a, cudaStream_t st) {
-    static uint64_t mask = 0;
-    constexpr size_t smem = gs_row_smem<NR>();
-    int rc = ensure_smem((const void*)k_gs_row<NR>, smem, &mask);
-    if (rc) return rc;
-    Launch ln("gs_row", st);
-    k_gs_row<NR><<<a.H / GsRowCfg<NR>::LPR, (NR / GsRowCfg<NR>::R) * GsRowCfg<NR>::LPR, smem, st>>>(a);
-    return ln.done("gs_row launch");
-}
-template <int NC>
-static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
-    static uint64_t mask0 = 0, mask1 = 0;
-    constexpr size_t smem = sizeof(float2) * size_t(GsColCfg<NC>::LPC) * gs_col_stride<NC>();
-    const int grid = a.W / GsColCfg<NC>::LPC, threads = (NC / GsColCfg<NC>::R) * GsColCfg<NC>::LPC;
-    int rc = last ? ensure_smem((const void*)k_gs_col<NC, true>, smem, &mask1)
-                  : ensure_smem((const void*)k_gs_col<NC, false>, smem, &mask0);
-    if (rc) return rc;
-    Launch ln("gs_col", st);
-    if (last) k_gs_col<NC, true><<<grid, threads, smem, st>>>(a);
-    else k_gs_col<NC, false><<<grid, threads, smem, st>>>(a);
-    return ln.done("gs_col launch");
+// Tile variants per shape. Defaults (GB300, 20 iterations, CUDA events): 1024^2 takes
+// column variant 0 and row variant 1 (20.5 us per iteration against 24.5 for 0/0),
+// 2048^2 column 1 and row 1 (75 against 106 us).
+struct GsTiles {
+    int col_v, row_v;
+};
+static std::mutex g_gs_mu;
+static std::map<std::pair<int, int>, GsTiles> g_gs_tiles;
+
+static GsTiles gs_tiles(int H, int W) {
+    {
+        std::lock_guard<std::mutex> lk(g_gs_mu);
+        auto it = g_gs_tiles.find({H, W});
+        if (it != g_gs_tiles.end()) return it->second;
+    }
+    GsTiles t;
+    t.col_v = H == 2048 ? 1 : 0;
+    t.row_v = (W == 1024 || W == 2048) ? 1 : 0;
+    return t;
 }
 
-#define HOLO_GS_SWITCH(n, CALL)                           \
+// every launch after k_gs_prepare may overlap the previous kernel's tail (pdl_wait first)
+template <int NC, int V>
+static int launch_col_init(const GsArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = gs_col_smem<NC, V>();
+    int rc = ensure_smem((const void*)k_gs_col_init<NC, V>, smem, &mask);
+    if (rc) return rc;
+    Launch ln("gs_col_init", st);
+    const cudaError_t le = launch_pdl(k_gs_col_init<NC, V>, dim3(a.W / GsColCfg<NC, V>::LPC), dim3((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC),
+               smem, st, a);
+    return ln.done("gs_col_init launch", le);
+}
+template <int NR, int V>
+static int launch_row(const GsArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = gs_row_smem<NR, V>();
+    int rc = ensure_smem((const void*)k_gs_row<NR, V>, smem, &mask);
+    if (rc) return rc;
+    Launch ln("gs_row", st);
+    const cudaError_t le = launch_pdl(k_gs_row<NR, V>, dim3(a.H / GsRowCfg<NR, V>::LPR), dim3((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR),
+               smem, st, a);
+    return ln.done("gs_row launch", le);
+}
+template <int NC, int V>
+static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
+    static uint64_t mask0 = 0, mask1 = 0;
+    constexpr size_t smem = sizeof(float2) * size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>();
+    const dim3 grid(a.W / GsColCfg<NC, V>::LPC), threads((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC);
+    int rc = last ? ensure_smem((const void*)k_gs_col<NC, V, true>, smem, &mask1)
+                  : ensure_smem((const void*)k_gs_col<NC, V, false>, smem, &mask0);
+    if (rc) return rc;
+    Launch ln("gs_col", st);
+    const cudaError_t le = last ? launch_pdl(k_gs_col<NC, V, true>, grid, threads, smem, st, a)
+                                : launch_pdl(k_gs_col<NC, V, false>, grid, threads, smem, st, a);
+    return ln.done("gs_col launch", le);
+}
+
+#define HOLO_GS_V(n, v, F) (v == 2 ? F(n, 2) : v == 1 ? F(n, 1) : F(n, 0))
+#define HOLO_GS_SWITCH(n, v, F)                           \
     switch (n) {                                          \
-        case 64: return CALL(64);                         \
-        case 128: return CALL(128);                       \
-        case 256: return CALL(256);                       \
-        case 512: return CALL(512);                       \
-        case 1024: return CALL(1024);                     \
-        case 2048: return CALL(2048);                     \
-        case 4096: return CALL(4096);                     \
+        case 64: return F(64, 0);                         \
+        case 128: return F(128, 0);                       \
+        case 256: return F(256, 0);                       \
+        case 512: return HOLO_GS_V(512, v, F);            \
+        case 1024: return HOLO_GS_V(1024, v, F);          \
+        case 2048: return HOLO_GS_V(2048, v, F);          \
+        case 4096: return F(4096, 0);                     \
         default: return fail(HOLO_EUNSUPPORTED, "line length %d", n); \
     }
 
-static int run_col_init(const GsArgs& a, cudaStream_t st) {
-#define C(n) launch_col_init<n>(a, st)
-    HOLO_GS_SWITCH(a.H, C)
+static int run_col_init(const GsArgs& a, int cv, cudaStream_t st) {
+#define C(n, v) launch_col_init<n, v>(a, st)
+    HOLO_GS_SWITCH(a.H, cv, C)
 #undef C
 }
-static int run_row(const GsArgs& a, cudaStream_t st) {
-#define C(n) launch_row<n>(a, st)
-    HOLO_GS_SWITCH(a.W, C)
+static int run_row(const GsArgs& a, int rv, cudaStream_t st) {
+#define C(n, v) launch_row<n, v>(a, st)
+    HOLO_GS_SWITCH(a.W, rv, C)
 #undef C
 }
-static int run_col(const GsArgs& a, bool last, cudaStream_t st) {
-#define C(n) launch_col<n>(a, last, st)
-    HOLO_GS_SWITCH(a.H, C)
+static int run_col(const GsArgs& a, int cv, bool last, cudaStream_t st) {
+#define C(n, v) launch_col<n, v>(a, last, st)
+    HOLO_GS_SWITCH(a.H, cv, C)
 #undef C
 }
-static int col_blocks(int H, int W) {
-    switch (H) {
-        case 64: return W / GsColCfg<64>::LPC;
-        case 128: return W / GsColCfg<128>::LPC;
-        case 256: return W / GsColCfg<256>::LPC;
-        case 512: return W / GsColCfg<512>::LPC;
-        case 1024: return W / GsColCfg<1024>::LPC;
-        case 2048: return W / GsColCfg<2048>::LPC;
-        default: return W / GsColCfg<4096>::LPC;
-    }
+static int col_blocks(int H, int W, int cv) {
+#define C(n, v) W / GsColCfg<n, v>::LPC
+    HOLO_GS_SWITCH(H, cv, C)
+#undef C
 }
 
 struct GsLayout {
@@ -314,7 +359,8 @@ static GsLayout gs_layout(int H, int W, int iters) {
     l.sc_off = align_up(P * sizeof(float2), 256);
     l.prep_off = l.sc_off + align_up(sizeof(GsScalars), 256);
     l.err_off = l.prep_off + align_up(sizeof(ff) * kGsPrepBlocks, 256);
-    l.total = l.err_off + align_up(sizeof(ff) * size_t(iters) * size_t(col_blocks(H, W)), 256);
+    // error partials for the column tiles with the fewest lines (any variant fits)
+    l.total = l.err_off + align_up(sizeof(ff) * size_t(iters) * size_t(W / kGsMinLpc), 256);
     return l;
 }
 
@@ -397,18 +443,21 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
                                                                reinterpret_cast<ff*>(ws + lay.prep_off));
         if ((rc = ln.done("gs_prepare launch"))) return rc;
     }
-    if ((rc = run_col_init(a, st))) return rc;
+    const GsTiles tiles = gs_tiles(H, W);
+    if ((rc = run_col_init(a, tiles.col_v, st))) return rc;
     for (int k = 0; k < iters; ++k) {
         const bool last = k == iters - 1;
         a.iter = k;
         a.codes_out = last ? d_phase_codes : nullptr;
-        if ((rc = run_row(a, st))) return rc;
-        if ((rc = run_col(a, last, st))) return rc;
+        if ((rc = run_row(a, tiles.row_v, st))) return rc;
+        if ((rc = run_col(a, tiles.col_v, last, st))) return rc;
     }
     if (d_err) {
+        const int nb = col_blocks(H, W, tiles.col_v);
+        if (nb < 1) return HOLO_EUNSUPPORTED;
         Launch ln("gs_finish", st);
-        k_gs_finish<<<iters, 32, 0, st>>>(a.err_part, col_blocks(H, W), d_err);
-        if ((rc = ln.done("gs_finish launch"))) return rc;
+        const cudaError_t le = launch_pdl(k_gs_finish, dim3(iters), dim3(32), 0, st, static_cast<const ff*>(a.err_part), nb, d_err);
+        if ((rc = ln.done("gs_finish launch", le))) return rc;
     }
     if (use_lut && L > 0) {
         bool prime = L >= 2;
@@ -416,5 +465,31 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
         if (!prime) warn("design rule: L=%lld is not prime", (long long)L);
         if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
     }
+    return HOLO_OK;
+}
+
+extern "C" int gs_tuning_set(int H, int W, int col_variant, int row_variant) {
+    clear_error();
+    int rc = gs_check_shape("gs_tuning_set", H, W);
+    if (rc) return rc;
+    if (col_variant < -1 || col_variant > 2 || row_variant < -1 || row_variant > 2)
+        return fail(HOLO_EINVAL, "gs_tuning_set: variants -1..2 (got %d, %d)", col_variant, row_variant);
+    std::lock_guard<std::mutex> lk(g_gs_mu);
+    if (col_variant < 0 || row_variant < 0) {
+        g_gs_tiles.erase({H, W});
+        return HOLO_OK;
+    }
+    g_gs_tiles[{H, W}] = GsTiles{gs_has_variants(H) ? col_variant : 0, gs_has_variants(W) ? row_variant : 0};
+    return HOLO_OK;
+}
+
+extern "C" int gs_tuning_get(int H, int W, int* col_variant, int* row_variant) {
+    clear_error();
+    int rc = gs_check_shape("gs_tuning_get", H, W);
+    if (rc) return rc;
+    if (!col_variant || !row_variant) return fail(HOLO_EINVAL, "gs_tuning_get: NULL output");
+    const GsTiles t = gs_tiles(H, W);
+    *col_variant = t.col_v;
+    *row_variant = t.row_v;
     return HOLO_OK;
 }

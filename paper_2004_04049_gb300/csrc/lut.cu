@@ -9,6 +9,7 @@ namespace holo {
 __global__ void k_lut_build(uint64_t seed, int64_t L, int bits, int cs_shift,
                             uint8_t* __restrict__ codes, float2* __restrict__ cs,
                             const float2* __restrict__ cs256) {
+    pdl_wait();   // a previous kernel may still read the table being rewritten
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < L; k += stride) {
         const uint32_t c = uint32_t(splitmix64_at(seed, uint64_t(k)) >> (64 - bits));
@@ -37,7 +38,7 @@ extern "C" int lut_build(uint64_t seed, int64_t L, int levels, uint8_t* d_codes,
     if (blocks > 152 * 32) blocks = 152 * 32;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
     Launch ln("lut_build", st);
-    k_lut_build<<<int(blocks), threads, 0, st>>>(seed, L, bits, 8 - bits, d_codes,
-                                                  reinterpret_cast<float2*>(d_cs), tab.cs256);
-    return ln.done("lut_build launch");
+    const cudaError_t le = launch_pdl(k_lut_build, dim3(int(blocks)), dim3(threads), 0, st, seed, L, bits, 8 - bits,
+                                      d_codes, reinterpret_cast<float2*>(d_cs), tab.cs256);
+    return ln.done("lut_build launch", le);
 }

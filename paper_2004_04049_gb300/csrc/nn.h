@@ -27,8 +27,14 @@ struct ConvArgs {
     int kchunk;                       // wgrad: pixels per split (set by conv3x3)
 };
 
-// mode: kConvFwd, kConvDgrad (forward kernel with flip = 1) or kConvWgrad
-int conv3x3(const ConvArgs& a, int mode, cudaStream_t st);
+// mode: kConvFwd, kConvDgrad (forward kernel with flip = 1) or kConvWgrad. Forward and
+// input gradient run on tcgen05 (nn_conv_tc05.cu) when the output width is 32, 64 or 128
+// and the tensors are 16-byte aligned; `legacy` forces the mma.sync kernel (comparisons).
+int conv3x3(const ConvArgs& a, int mode, cudaStream_t st, bool legacy = false);
+bool conv3x3_tc05_supported(const ConvArgs& a);
+int conv3x3_tc05(const ConvArgs& a, int mode, cudaStream_t st);
+// reads (and optionally clears) the flag a tcgen05 conv kernel sets when a bounded wait expires
+int conv3x3_tc05_fault(int* out, bool clear);
 
 // ---- elementwise / reductions (nn_ops.cu); tensors are [B][H][W][C] bf16, C % 8 == 0
 int prep_input(const float* target, int B, int Hs, int Ws, int H, int W, __nv_bfloat16* x, int C,

@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a) {
             }
 }
 
-int conv3x3(const ConvArgs& a, int mode, cudaStream_t st) {
+int conv3x3(const ConvArgs& a, int mode, cudaStream_t st, bool legacy) {
     if (a.Cin % 8 || a.Cout % 8) return fail(HOLO_EINVAL, "conv3x3: channels must be multiples of 8");
+    if (mode != kConvWgrad && !legacy && conv3x3_tc05_supported(a)) return conv3x3_tc05(a, mode, st);
     const int P = a.B * a.H * a.W;
     if (mode == kConvWgrad) {
         ConvArgs b = a;

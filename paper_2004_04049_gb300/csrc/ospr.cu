@@ -37,6 +37,7 @@ namespace holo {
 // first half of the raster (rows 0 .. H/2) whose mirror lies at or after it.
 __global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, int W,
                                 float scale, float* __restrict__ I) {
+    pdl_wait();
     const size_t P = size_t(H) * W;
     const size_t half = P / 2 + W;             // rows 0 .. H/2 inclusive
     const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -212,8 +213,9 @@ static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_repla
         const int threads = 256;
         const int blocks = int((P / 2 + a.W + threads - 1) / threads);
         Launch ln("ospr_finalize", st);
-        k_ospr_finalize<<<blocks, threads, 0, st>>>(a.sacc, pl.groups, a.H, a.W, scale, d_replay);
-        if ((rc = ln.done("ospr_finalize launch"))) return rc;
+        const cudaError_t le = launch_pdl(k_ospr_finalize, dim3(blocks), dim3(threads), 0, st,
+                                          static_cast<const float*>(a.sacc), pl.groups, a.H, a.W, scale, d_replay);
+        if ((rc = ln.done("ospr_finalize launch", le))) return rc;
     }
     return HOLO_OK;
 }

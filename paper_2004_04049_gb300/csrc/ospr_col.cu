@@ -12,8 +12,8 @@ static int launch_col_ifft(const OsprArgs& a, cudaStream_t st) {
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC, V>::LPC, a.pairs);
     Launch ln("ospr_col_ifft", st);
-    k_ospr_col_ifft<NC, V, 0><<<grid, (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC, smem, st>>>(a);
-    return ln.done("ospr_col_ifft launch");
+    const cudaError_t le = launch_pdl(k_ospr_col_ifft<NC, V, 0>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
+    return ln.done("ospr_col_ifft launch", le);
 }
 
 template <int NC, int V>
@@ -24,8 +24,8 @@ static int launch_col_fft(const OsprArgs& a, cudaStream_t st) {
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC, V>::LPC, a.groups);
     Launch ln("ospr_col_fft", st);
-    k_ospr_col_fft<NC, V, 0><<<grid, (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC, smem, st>>>(a);
-    return ln.done("ospr_col_fft launch");
+    const cudaError_t le = launch_pdl(k_ospr_col_fft<NC, V, 0>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
+    return ln.done("ospr_col_fft launch", le);
 }
 
 #define HOLO_COL_VARIANTS(N, v, F) \

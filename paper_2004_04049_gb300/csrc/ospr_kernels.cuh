@@ -290,6 +290,7 @@ k_ospr_col_ifft(OsprArgs a) {
     float2* cs = sm;
     float2* lines = sm + kCsSmemEntries;
     load_cs_table(cs, a.cs256);
+    pdl_wait();   // the table and target may be written by the previous kernel
     __syncthreads();
 
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
@@ -318,6 +319,7 @@ k_ospr_col_ifft(OsprArgs a) {
             if (t > 0 || e > R / 2) v[e] = own[pad_index<R>(t + T * e)];
     }
     col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
+    pdl_trigger();
     float2* z = a.zbuf + size_t(blockIdx.y) * size_t(NC) * size_t(W);
 #pragma unroll
     for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
@@ -337,6 +339,7 @@ k_ospr_row(OsprArgs a) {
     const bool single = s0 + 1 >= a.N;
     const size_t P = size_t(a.H) * NR;
     float2* z = a.zbuf + size_t(blockIdx.y) * P + size_t(r) * NR;
+    pdl_wait();
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
@@ -360,6 +363,7 @@ k_ospr_row(OsprArgs a) {
     }
     if constexpr (REPLAY) {
         row_line_fft<NR, V, -1, PREC>(v, sm, line, t, a);
+        pdl_trigger();
 #pragma unroll
         for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
     }
@@ -376,6 +380,7 @@ k_ospr_col_fft(OsprArgs a) {
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
     const size_t P = size_t(NC) * W;
+    pdl_wait();
     float acc[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) acc[e] = 0.f;
@@ -388,6 +393,7 @@ k_ospr_col_fft(OsprArgs a) {
 #pragma unroll
         for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
     }
+    pdl_trigger();
     float* S = a.sacc + size_t(blockIdx.y) * P;
 #pragma unroll
     for (int e = 0; e < R; ++e) {

@@ -12,8 +12,8 @@ static int launch_row(const OsprArgs& a, cudaStream_t st) {
     if (rc) return rc;
     dim3 grid(a.H / RowCfg<NR, V>::LPR, a.pairs);
     Launch ln("ospr_row", st);
-    k_ospr_row<NR, V, REPLAY, 0><<<grid, (NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR, smem, st>>>(a);
-    return ln.done("ospr_row launch");
+    const cudaError_t le = launch_pdl(k_ospr_row<NR, V, REPLAY, 0>, grid, dim3((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR), smem, st, a);
+    return ln.done("ospr_row launch", le);
 }
 
 template <int NR, int V>

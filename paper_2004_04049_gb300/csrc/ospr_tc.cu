@@ -13,8 +13,8 @@ static int launch_col_ifft_tc(const OsprArgs& a, cudaStream_t st) {
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC, V>::LPC, a.pairs);
     Launch ln("ospr_col_ifft", st);
-    k_ospr_col_ifft<NC, V, PREC><<<grid, (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC, smem, st>>>(a);
-    return ln.done("ospr_col_ifft launch");
+    const cudaError_t le = launch_pdl(k_ospr_col_ifft<NC, V, PREC>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
+    return ln.done("ospr_col_ifft launch", le);
 }
 
 template <int NC, int PREC>
@@ -26,8 +26,8 @@ static int launch_col_fft_tc(const OsprArgs& a, cudaStream_t st) {
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC, V>::LPC, a.groups);
     Launch ln("ospr_col_fft", st);
-    k_ospr_col_fft<NC, V, PREC><<<grid, (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC, smem, st>>>(a);
-    return ln.done("ospr_col_fft launch");
+    const cudaError_t le = launch_pdl(k_ospr_col_fft<NC, V, PREC>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
+    return ln.done("ospr_col_fft launch", le);
 }
 
 template <int NR, int PREC, bool REPLAY>
@@ -39,8 +39,8 @@ static int launch_row_tc(const OsprArgs& a, cudaStream_t st) {
     if (rc) return rc;
     dim3 grid(a.H / RowCfg<NR, V>::LPR, a.pairs);
     Launch ln("ospr_row", st);
-    k_ospr_row<NR, V, REPLAY, PREC><<<grid, (NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR, smem, st>>>(a);
-    return ln.done("ospr_row launch");
+    const cudaError_t le = launch_pdl(k_ospr_row<NR, V, REPLAY, PREC>, grid, dim3((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR), smem, st, a);
+    return ln.done("ospr_row launch", le);
 }
 
 int ospr_run_col_ifft_tc(const OsprArgs& a, int prec, cudaStream_t st) {

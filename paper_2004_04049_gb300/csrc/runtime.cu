@@ -85,8 +85,9 @@ Launch::Launch(const char* family, cudaStream_t stream) : family_(family), strea
     }
 }
 
-int Launch::done(const char* what) {
+int Launch::done(const char* what, cudaError_t launch) {
     cudaError_t e = cudaGetLastError();
+    if (launch != cudaSuccess) e = launch;
     if (e != cudaSuccess) return cuda_status(e, what);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (start_) {

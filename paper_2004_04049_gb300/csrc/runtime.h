@@ -27,7 +27,8 @@ int cuda_status(cudaError_t e, const char* what);
 class Launch {
   public:
     Launch(const char* family, cudaStream_t stream);
-    int done(const char* what);
+    // `launch` is the status a cudaLaunchKernelEx call returned (cudaSuccess for <<<>>>)
+    int done(const char* what, cudaError_t launch = cudaSuccess);
   private:
     const char* family_;
     cudaStream_t stream_;
@@ -36,6 +37,36 @@ class Launch {
 
 // Sets event profiling on or off and returns the previous setting.
 int profiling_swap(int on);
+
+// ---- programmatic dependent launch ------------------------------------------------
+// A kernel launched with launch_pdl may be scheduled while the previous kernel on its
+// stream is still running, which hides the launch latency between dependent kernels.
+// It must execute pdl_wait() before its first access to memory that earlier work on the
+// stream writes or reads (griddepcontrol.wait returns once the preceding grid has
+// completed and its writes are visible; it returns at once when there is none), and
+// may execute pdl_trigger() once its own CTAs no longer need the slots the next
+// kernel's CTAs would take (the next kernel launches when every CTA has triggered or
+// exited).
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // ---- constant tables ---------------------------------------------------------
 struct TcFrags;

@@ -515,6 +515,8 @@ extern "C" int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, cons
                           const void* d_dy, const float* d_bias, const void* d_residual, int relu, void* d_out,
                           float* d_out_f32, float* d_dw, holo_stream_t s) {
     clear_error();
+    const bool legacy = (mode & HOLO_CONV_LEGACY) != 0;
+    mode &= ~HOLO_CONV_LEGACY;
     if (mode < 0 || mode > 2 || B < 1 || H < 1 || W < 1 || Cin < 8 || Cout < 8 || Cin % 8 || Cout % 8 || !d_in)
         return fail(HOLO_EINVAL, "nn_conv3x3: bad arguments");
     ConvArgs a{};
@@ -535,5 +537,11 @@ extern "C" int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, cons
     a.dw = d_dw;
     if (mode != kConvWgrad && (!d_wmat || (!d_out && !d_out_f32))) return fail(HOLO_EINVAL, "nn_conv3x3: outputs");
     if (mode == kConvWgrad && (!d_dy || !d_dw)) return fail(HOLO_EINVAL, "nn_conv3x3: wgrad needs dy and dw");
-    return conv3x3(a, mode, reinterpret_cast<cudaStream_t>(s));
+    return conv3x3(a, mode, reinterpret_cast<cudaStream_t>(s), legacy);
+}
+
+extern "C" int nn_tc_status(int* fault, int clear) {
+    clear_error();
+    if (!fault) return fail(HOLO_EINVAL, "nn_tc_status: NULL output");
+    return conv3x3_tc05_fault(fault, clear != 0);
 }

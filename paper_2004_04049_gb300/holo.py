@@ -86,6 +86,8 @@ _SIGS = {
     "ospr_tuning_get": (_c.c_int, [_c.c_int, _c.c_int] + [_c.POINTER(_c.c_int)] * 5),
     "ospr_tuning_set": (_c.c_int, [_c.c_int] * 7),
     "gs_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "gs_tuning_set": (_c.c_int, [_c.c_int] * 4),
+    "gs_tuning_get": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "gs_iterate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
                               _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
                               _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
@@ -106,6 +108,7 @@ _SIGS = {
     "nn_conv3x3": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.c_void_p,
                               _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p,
                               _c.c_void_p, _c.c_void_p]),
+    "nn_tc_status": (_c.c_int, [_c.POINTER(_c.c_int), _c.c_int]),
     "replay_error_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "replay_error": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int,
                                 _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
@@ -291,6 +294,17 @@ def ospr_tuning_set(H, W, col_ifft_variant=0, col_fft_variant=0, row_variant=0, 
     return _call("ospr_tuning_set", H, W, col_ifft_variant, col_fft_variant, row_variant, chunk, groups)
 
 
+def gs_tuning_set(H, W, col_variant=-1, row_variant=-1):
+    """Tile variants of the GS passes for this shape; -1 restores the defaults."""
+    return _call("gs_tuning_set", H, W, col_variant, row_variant)
+
+
+def gs_tuning_get(H, W):
+    v = [ctypes.c_int(0) for _ in range(2)]
+    _call("gs_tuning_get", H, W, *[ctypes.byref(x) for x in v])
+    return {"col_variant": v[0].value, "row_variant": v[1].value}
+
+
 def gs_workspace_size(H, W, iters, precision=HOLO_FP32):
     b = ctypes.c_size_t(0)
     _call("gs_workspace_size", H, W, iters, precision, ctypes.byref(b))
@@ -403,3 +417,13 @@ def nn_conv3x3(mode, B, H, W, Cin, Cout, d_in, d_wmat=None, d_dy=None, d_bias=No
     return _call("nn_conv3x3", mode, B, H, W, Cin, Cout, _ptr(d_in), _ptr(d_wmat), _ptr(d_dy), _ptr(d_bias),
                  _ptr(d_residual), 1 if relu else 0, _ptr(d_out), _ptr(d_out_f32), _ptr(d_dw),
                  _stream(stream, d_in))
+
+
+HOLO_CONV_LEGACY = 16
+
+
+def nn_tc_status(clear=False):
+    """1 if a tcgen05 convolution kernel gave up on a bounded wait since the last clear."""
+    v = ctypes.c_int(0)
+    _call("nn_tc_status", ctypes.byref(v), 1 if clear else 0)
+    return v.value

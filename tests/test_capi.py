@@ -113,3 +113,17 @@ def test_tuning_set_get_host_only(lib):
     finally:
         holo.ospr_tuning_set(256, 512)
         holo.ospr_tuning_set(1024, 1024)
+
+
+def test_gs_tuning_host_only(lib):
+    assert holo.gs_tuning_get(1024, 1024) == {"col_variant": 0, "row_variant": 1}
+    assert holo.gs_tuning_get(2048, 2048) == {"col_variant": 1, "row_variant": 1}
+    holo.gs_tuning_set(256, 1024, 2, 2)   # 256-point columns have one variant
+    try:
+        assert holo.gs_tuning_get(256, 1024) == {"col_variant": 0, "row_variant": 2}
+        with pytest.raises(holo.HoloError) as ei:
+            holo.gs_tuning_set(256, 1024, 3, 0)
+        assert ei.value.status == holo.HOLO_EINVAL
+    finally:
+        holo.gs_tuning_set(256, 1024)
+    assert holo.gs_tuning_get(256, 1024) == {"col_variant": 0, "row_variant": 1}

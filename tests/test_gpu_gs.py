@@ -13,7 +13,7 @@ import torch
 from oracle import fft as offt
 from oracle import gs as ogs
 from oracle import lut as olut
-from paper_2004_04049_gb300 import pipeline
+from paper_2004_04049_gb300 import holo, pipeline
 from parity import NMSE_REL, REPLAY_REL, check_codes, check_replay
 from synthetic import blob_target, noise_target
 
@@ -30,6 +30,21 @@ def _init_state(T, L, seed):
                                              (128, 512, 256, "blob"), (256, 128, 2, "blob"),
                                              (1024, 1024, 256, "blob")])
 def test_single_iteration_parity(cuda, H, W, levels, kind):
+    _single_iteration(cuda, H, W, levels, kind)
+
+
+@pytest.mark.parametrize("H,W", [(512, 1024), (2048, 512)])
+@pytest.mark.parametrize("tiles", [(0, 0), (1, 2), (2, 1), (1, 1)])
+def test_tile_variants_parity(cuda, H, W, tiles):
+    holo.gs_tuning_set(H, W, *tiles)
+    try:
+        assert holo.gs_tuning_get(H, W) == {"col_variant": tiles[0], "row_variant": tiles[1]}
+        _single_iteration(cuda, H, W, 256, "noise")
+    finally:
+        holo.gs_tuning_set(H, W)
+
+
+def _single_iteration(cuda, H, W, levels, kind):
     T = blob_target(H, W, 1010) if kind == "blob" else noise_target(H, W, 2010)
     E32 = _init_state(T, 10007, 3)
     t = torch.from_numpy(T).to(cuda)
@@ -52,7 +67,12 @@ def test_single_iteration_parity(cuda, H, W, levels, kind):
     assert abs(geps[0] - eps) <= 10 * NMSE_REL * eps, (geps[0], eps)
     En = ogs.amplitude_constraint(R, Ts)
     gEc = gE[..., 0] + 1j * gE[..., 1]
-    assert np.abs(gEc - En).max() <= REPLAY_REL * np.abs(En).max()
+    # E = T_s exp(i arg R): an error dR in the float32 replay field turns the phase by up to
+    # |dR|/|R|, so the state error at a pixel is bounded by T_s |dR| / |R| (ill-conditioned
+    # where R nearly vanishes) plus the rounding of E itself
+    dR = REPLAY_REL * np.abs(R).max()
+    bound = Ts * np.minimum(2.0, dR / np.maximum(np.abs(R), 1e-30)) + REPLAY_REL * np.abs(En).max()
+    assert np.all(np.abs(gEc - En) <= bound), np.max(np.abs(gEc - En) / bound)
 
 
 @pytest.mark.parametrize("levels", [256, 2])

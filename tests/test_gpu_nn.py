@@ -40,7 +40,35 @@ def test_conv_forward(cuda, B, H, W, Ci, Co):
     assert np.max(np.abs(g - ref)) <= 1e-5 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("B,H,W,Ci,Co", [(2, 16, 16, 16, 24), (1, 32, 8, 64, 8)])
+# tcgen05 path: output widths 32/64/128, pixel counts that leave a partial 128-pixel tile,
+# K = 9*Cin that leaves a partial 64-element slice, batches that cross images in one tile
+@pytest.mark.parametrize("B,H,W,Ci,Co", [(1, 24, 24, 40, 128), (3, 10, 14, 8, 32), (2, 64, 64, 64, 64),
+                                         (1, 8, 16, 128, 128)])
+@pytest.mark.parametrize("legacy", [False, True])
+def test_conv_forward_tcgen05_and_legacy(cuda, B, H, W, Ci, Co, legacy):
+    rng = np.random.default_rng(B * 1000 + H * 10 + Ci)
+    x = bf16_round(rng.standard_normal((B, H, W, Ci)))
+    w = bf16_round(rng.standard_normal((Co, 3, 3, Ci)) * 0.1)
+    b = rng.standard_normal(Co).astype(np.float32)
+    res = bf16_round(rng.standard_normal((B, H, W, Co)))
+    out = torch.zeros((B, H, W, Co), dtype=torch.float32, device=cuda)
+    outb = torch.zeros((B, H, W, Co), dtype=torch.bfloat16, device=cuda)
+    mode = holo.HOLO_CONV_LEGACY if legacy else 0
+    holo.nn_tc_status(clear=True)
+    holo.nn_conv3x3(mode, B, H, W, Ci, Co, _dev_bf16(x, cuda), _dev_bf16(w.reshape(Co, -1), cuda),
+                    d_bias=torch.from_numpy(b).to(cuda), d_residual=_dev_bf16(res, cuda), relu=True,
+                    d_out=outb, d_out_f32=out)
+    torch.cuda.synchronize()
+    assert holo.nn_tc_status() == 0
+    ref = np.maximum(oc.conv3x3(x, w, b) + res, 0.0)
+    g = out.cpu().numpy()
+    assert np.max(np.abs(g - ref)) <= 1e-5 * max(1.0, np.abs(ref).max())
+    # the bf16 output is the float32 result rounded to nearest even
+    assert torch.equal(outb.cpu(), out.cpu().to(torch.bfloat16))
+
+
+@pytest.mark.parametrize("B,H,W,Ci,Co", [(2, 16, 16, 16, 24), (1, 32, 8, 64, 8), (2, 20, 12, 128, 32),
+                                         (1, 16, 16, 32, 128)])
 def test_conv_input_gradient(cuda, B, H, W, Ci, Co):
     rng = np.random.default_rng(7 + Ci)
     dy = bf16_round(rng.standard_normal((B, H, W, Co)))
