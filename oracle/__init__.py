@@ -11,6 +11,7 @@ Modules
 -------
 fft    unitary 2D DFT / IDFT (Eq. 1, Eq. 2): brute-force definition and radix-2 FFT.
 lut    the phase LUT "pool" (Section 4) drawn cyclically with continuation (Section 5, Fig. 3).
+lfsr   m-sequence phase codes, the PRNG alternative Section 7 compares the LUT with.
 ospr   One-Step Phase-Retrieval with binary sub-frames (Section 2, Section 3).
 gs     Gerchberg-Saxton with a phase-quantised hologram (Section 2).
 error  MSE / NMSE of a replay field against its target (Section 5.2, Eq. 3).
@@ -20,4 +21,4 @@ Readings of points the paper leaves open are listed in the design notes and repe
 each function's docstring.
 """
 
-from . import conv, fft, lut, ospr, gs, error  # noqa: F401
+from . import conv, fft, lfsr, lut, ospr, gs, error  # noqa: F401
