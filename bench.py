@@ -419,6 +419,7 @@ def run_ours(args):
 
     batch = run_batch_leg(dev, stream) if not args.no_batch else None
     precision_leg = run_precision_leg(dev, stream) if not args.no_batch else None
+    sources_leg = run_phase_source_leg(dev, stream) if not args.no_batch else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -454,6 +455,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 4 * P + 24)},
             "batch": batch,
             "precision": precision_leg,
+            "phase_sources": sources_leg,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -541,6 +543,66 @@ def run_batch_leg(dev, stream, reps=3):
             "per_frame_launches": sub / (t_pf / 1e3), "batch_call": sub / (t_batch / 1e3),
             "graph_launch": sub / (t_graph / 1e3), "ms": {"per_frame": t_pf, "batch": t_batch, "graph": t_graph},
             "tuning": tunings}
+
+
+# ----------------------------------------------------------- phase sources leg ----
+def run_phase_source_leg(dev, stream, reps=10):
+    """One 1024x1024 N=24 frame (lut/lfsr build + ospr_generate + replay_error) with the
+    phases from the paper's LUT (L = 10007), from an m-sequence (Section 7's alternative:
+    a fresh code for every pixel of every sub-frame, built per frame) and from the
+    counter-based SplitMix64 generator (no table)."""
+    import torch
+
+    from paper_2004_04049_gb300 import holo, pipeline
+    from synthetic import blob_target
+
+    s = stream.cuda_stream
+    P = H * W
+    T = torch.from_numpy(blob_target(H, W, 1000)).to(dev)
+    ws = torch.empty(holo.ospr_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
+    ews = torch.empty(holo.replay_error_workspace_size(H, W), dtype=torch.uint8, device=dev)
+    bits = torch.empty((N_SF, P // 32), dtype=torch.int32, device=dev)
+    I = torch.empty((H, W), dtype=torch.float32, device=dev)
+    err = torch.empty(3, dtype=torch.float64, device=dev)
+    lut = torch.empty(GS_L, dtype=torch.uint8, device=dev)
+    mseq = torch.empty(N_SF * P, dtype=torch.uint8, device=dev)
+    frame_no = [0]
+
+    def run(kind):
+        f = frame_no[0]
+        frame_no[0] += 1
+        if kind == "lut":
+            holo.lut_build(LUT_SEED, GS_L, 256, lut, None, stream=s)
+            pipeline.ospr(T, N_SF, lut, GS_L, 256, LUT_SEED, 0, 0, ws=ws, out_bits=bits, out_replay=I, stream=s)
+        elif kind == "m_sequence":
+            holo.lfsr_build(0x1D872B41, f * N_SF * P, N_SF * P, 256, mseq, stream=s)
+            pipeline.ospr(T, N_SF, mseq, N_SF * P, 256, 0, 0, 0, ws=ws, out_bits=bits, out_replay=I, stream=s)
+        else:
+            pipeline.ospr(T, N_SF, None, holo.L_UNREPEATED, 256, LUT_SEED + f, 0, 0, ws=ws, out_bits=bits,
+                          out_replay=I, stream=s)
+        pipeline.error(I, T, ws=ews, out=err, stream=s)
+
+    out = {}
+    for kind in ("lut", "m_sequence", "splitmix64"):
+        for _ in range(3):
+            run(kind)
+        torch.cuda.synchronize(dev)
+        holo.holo_profile_reset()
+        holo.holo_profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run(kind)
+        e1.record(stream)
+        e1.synchronize()
+        holo.holo_profile_enable(False)
+        ms = e0.elapsed_time(e1) / reps
+        build = holo.holo_profile_read("lut_build" if kind == "lut" else "lfsr_build")
+        gen = holo.holo_profile_read("ospr_col_ifft")
+        out[kind] = {"ms_per_frame": ms, "subframes_per_s": N_SF / (ms / 1e3), "nmse": float(err[2].item()),
+                     "table_build_us": build[1] / max(build[0], 1) * 1e3 if kind != "splitmix64" else 0.0,
+                     "generation_pass_us": gen[1] / max(gen[0], 1) * 1e3}
+    return out
 
 
 # --------------------------------------------------------- mixed precision leg ----
@@ -732,6 +794,47 @@ def conv_throughput(reps=20):
     return out
 
 
+def gs_tile_sweep(sizes=(1024, 2048), iters=20, reps=10):
+    """GS time per iteration for every (column, row) tile variant pair (gs_tuning_set)."""
+    import torch
+
+    from paper_2004_04049_gb300 import holo, pipeline
+    from synthetic import blob_target
+
+    dev = torch.device("cuda:0")
+    s = torch.cuda.current_stream(dev).cuda_stream
+    rows = []
+    for n in sizes:
+        T = torch.from_numpy(blob_target(n, n, 1000)).to(dev)
+        codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
+        ws = torch.empty(holo.gs_workspace_size(n, n, iters), dtype=torch.uint8, device=dev)
+        q = torch.empty((n, n), dtype=torch.uint8, device=dev)
+        I = torch.empty((n, n), dtype=torch.float32, device=dev)
+        err = torch.empty(iters, dtype=torch.float64, device=dev)
+        for cv in range(3):
+            for rv in range(3):
+                holo.gs_tuning_set(n, n, cv, rv)
+
+                def f():
+                    holo.gs_iterate(T, n, n, iters, 256, None, codes, GS_L, 256, LUT_SEED, 0, 0, q, I, err, None,
+                                    None, ws, ws.numel(), stream=s)
+
+                for _ in range(3):
+                    f()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    f()
+                e1.record()
+                e1.synchronize()
+                us = e0.elapsed_time(e1) / reps / iters * 1e3
+                rows.append({"n": n, "col_variant": cv, "row_variant": rv, "us_per_iter": us,
+                             "iter_per_s": 1e6 / us, "eps_last": float(err[-1].item()) / (n * n)})
+        holo.gs_tuning_set(n, n)
+    return rows
+
+
 def run_learned(args):
     """Learned GS warm start at the configured scale (labels from 100-iteration GS on 20k
     seeded 256^2 targets, training by the library's kernels, evaluation at 1024^2), plus
@@ -796,6 +899,9 @@ def main():
     ap.add_argument("--learned-n", type=int, default=20000)
     ap.add_argument("--learned-epochs", type=int, default=2)
     ap.add_argument("--conv", action="store_true", help="time the network's convolution kernels only")
+    ap.add_argument("--study", action="store_true", help="run the LUT-length study of Figs. 5-6")
+    ap.add_argument("--gs-tiles", action="store_true", help="time GS for every tile variant pair")
+    ap.add_argument("--study-runs", type=int, default=100)
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="store per-launch DRAM bytes from an ncu --csv log in profiles/dram_traffic.json")
     ap.add_argument("--traffic-command", default="", help="the ncu command that wrote the CSV")
@@ -806,6 +912,22 @@ def main():
         return
     if args.learned:
         run_learned(args)
+        return
+    if args.study:
+        from paper_2004_04049_gb300 import build_lib, holo, study
+        build_lib.build()
+        holo.load()
+        t0 = time.perf_counter()
+        res = study.lut_length_study(sizes=(256, 128, 64), N=24, runs=args.study_runs, n_targets=6,
+                                     log=lambda m: print(m, file=sys.stderr))
+        print(json.dumps({"study": "LUT length vs NMSE ratio (Section 5.2, Figs. 5-6), synthetic targets",
+                          "seconds": time.perf_counter() - t0, "results": res}), flush=True)
+        return
+    if args.gs_tiles:
+        from paper_2004_04049_gb300 import build_lib, holo
+        build_lib.build()
+        holo.load()
+        print(json.dumps({"gs_tiles": gs_tile_sweep()}), flush=True)
         return
     if args.conv:
         from paper_2004_04049_gb300 import build_lib, holo

@@ -76,7 +76,7 @@ int holo_launch_count(uint64_t* out_count);
  * for the kernel family `name`, the number of launches and their summed duration in
  * milliseconds since the last holo_profile_reset. Families: "lut_build",
  * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "gs_prepare",
- * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2",
+ * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2", "lfsr_build",
  * "nn_conv_fwd", "nn_conv_dgrad", "nn_conv_wgrad", "nn_elementwise",
  * "nn_loss", "nn_adam". */
 int holo_profile_enable(int on);
@@ -100,6 +100,25 @@ int holo_profile_read(const char* name, uint64_t* launches, double* total_ms);
  */
 int lut_build(uint64_t seed, int64_t L, int levels, uint8_t* d_codes, float* d_cs,
               holo_stream_t s);
+
+/*
+ * lfsr_build - m-sequence phase codes: the PRNG alternative Section 7 weighs against the
+ * LUT (an m-sequence generator feeding a cos/sin table). Not part of the paper's method;
+ * provided to compare the two on error and speed.
+ *
+ * Galois LFSR with the primitive polynomial x^31 + x^3 + 1: state s_k = seed_state * x^k
+ * mod p, output bit b_k = coefficient of x^30 of s_k (period 2^31 - 1). Writes
+ * d_codes[k] = code(start + k), k < count, where code i packs bits b_{m i} ..
+ * b_{m i + m - 1} (m = log2(levels)) most significant first. The result is a table for the
+ * table mode of ospr_generate / gs_iterate (L = count): with count >= N*H*W every pixel of
+ * every sub-frame draws its own m-sequence code (start = the frame's first draw).
+ *
+ *   seed_state  1 .. 2^31 - 1.   start  0 .. 2^56.   count 1 .. 2^31 - 1.
+ *   levels      power of two in [2, 256].   d_codes  [count] uint8, device, caller-owned.
+ * Errors: HOLO_EINVAL, HOLO_ECUDA. Asynchronous on s.
+ */
+int lfsr_build(uint32_t seed_state, int64_t start, int64_t count, int levels, uint8_t* d_codes,
+               holo_stream_t s);
 
 /* ------------------------------------------------------------------- OSPR ---- */
 
@@ -373,7 +392,8 @@ int ws_load(ws_net* net, const char* path);
  * nn_conv3x3 - the network's convolution kernel on its own (3x3, zero padding 1, stride
  * 1, channels-last bf16 tensors, channels multiples of 8, float32 accumulation). Modes 0
  * and 1 run on the tcgen05 tensor cores (accumulator in tensor memory) when the output
- * width is 32, 64 or 128 and every tensor is 16-byte aligned, else on the mma.sync kernel;
+ * width is 32, 64 or 128, the input has at least 32 channels and every tensor is 16-byte
+ * aligned, else on the mma.sync kernel;
  * mode | HOLO_CONV_LEGACY forces the mma.sync kernel (for comparisons). Mode 2 always
  * uses the mma.sync kernel.
  *   mode 0 forward: d_out[p][o] = act(sum X(p,k) W[o][k] + bias[o] + residual[p][o]) with

@@ -28,8 +28,9 @@ struct ConvArgs {
 };
 
 // mode: kConvFwd, kConvDgrad (forward kernel with flip = 1) or kConvWgrad. Forward and
-// input gradient run on tcgen05 (nn_conv_tc05.cu) when the output width is 32, 64 or 128
-// and the tensors are 16-byte aligned; `legacy` forces the mma.sync kernel (comparisons).
+// input gradient run on tcgen05 (nn_conv_tc05.cu) when the output width is 32, 64 or 128,
+// the input has at least 32 channels and the tensors are 16-byte aligned; `legacy` forces
+// the mma.sync kernel (comparisons).
 int conv3x3(const ConvArgs& a, int mode, cudaStream_t st, bool legacy = false);
 bool conv3x3_tc05_supported(const ConvArgs& a);
 int conv3x3_tc05(const ConvArgs& a, int mode, cudaStream_t st);

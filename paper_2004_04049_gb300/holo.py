@@ -67,6 +67,7 @@ _SIGS = {
     "holo_profile_reset": (_c.c_int, []),
     "holo_profile_read": (_c.c_int, [_c.c_char_p, _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_double)]),
     "lut_build": (_c.c_int, [_c.c_uint64, _c.c_int64, _c.c_int, _c.c_void_p, _c.c_void_p, _c.c_void_p]),
+    "lfsr_build": (_c.c_int, [_c.c_uint32, _c.c_int64, _c.c_int64, _c.c_int, _c.c_void_p, _c.c_void_p]),
     "ospr_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "ospr_generate": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int,
                                  _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
@@ -210,6 +211,11 @@ def holo_profile_read(name):
 # ------------------------------------------------------------------- compute ----
 def lut_build(seed, L, levels, d_codes, d_cs=None, stream=None):
     return _call("lut_build", seed, L, levels, _ptr(d_codes), _ptr(d_cs), _stream(stream, d_codes))
+
+
+def lfsr_build(seed_state, start, count, levels, d_codes, stream=None):
+    """m-sequence codes start .. start+count-1 into d_codes (a table for table mode)."""
+    return _call("lfsr_build", seed_state, start, count, levels, _ptr(d_codes), _stream(stream, d_codes))
 
 
 def ospr_workspace_size(H, W, N, precision=HOLO_FP32):

@@ -127,3 +127,12 @@ def test_gs_tuning_host_only(lib):
     finally:
         holo.gs_tuning_set(256, 1024)
     assert holo.gs_tuning_get(256, 1024) == {"col_variant": 0, "row_variant": 1}
+
+
+def test_lfsr_build_validation_host_only(lib):
+    for args in [(0, 0, 16, 256), (1 << 31, 0, 16, 256), (1, -1, 16, 256), (1, 0, 0, 256), (1, 0, 16, 3)]:
+        with pytest.raises(holo.HoloError) as ei:
+            holo.lfsr_build(*args, 1 << 20)
+        assert ei.value.status == holo.HOLO_EINVAL
+    with pytest.raises(holo.HoloError):
+        holo.lfsr_build(1, 0, 16, 256, None)

@@ -131,15 +131,18 @@ def test_global_phase_equivariance(cuda):
     assert np.allclose(a["err"].cpu().numpy(), b["err"].cpu().numpy(), rtol=1e-5)
 
 
-def test_caller_phase_equals_lut_phase(cuda):
+# start index k*P + j: frame k of a GS video continues the table draw (Fig. 3 continuation;
+# Section 8 allows LUT reuse across frames when L is prime and longer than the image side)
+@pytest.mark.parametrize("start", [0, 5 * 128 * 128 + 17])
+def test_caller_phase_equals_lut_phase(cuda, start):
     H = W = 128
     T = blob_target(H, W, 1014)
     t = torch.from_numpy(T).to(cuda)
     L, seed = 521, 8
     codes = pipeline.lut(seed, L, device=cuda)
-    theta = olut.phase_of_codes(olut.subframe_codes(olut.lut_codes(seed, L), L, seed, 0, 0,
+    theta = olut.phase_of_codes(olut.subframe_codes(olut.lut_codes(seed, L), L, seed, start, 0,
                                                     H * W, H * W)).reshape(H, W)
-    a = pipeline.gs(t, 1, 256, codes, L, 256, seed)
+    a = pipeline.gs(t, 1, 256, codes, L, 256, seed, start=start)
     b = pipeline.gs(t, 1, 256, init_phase=torch.from_numpy(theta.astype(np.float32)).to(cuda))
     qa, qb = a["codes"].cpu().numpy(), b["codes"].cpu().numpy()
     assert np.mean(qa == qb) >= 0.9999

@@ -42,8 +42,8 @@ def test_conv_forward(cuda, B, H, W, Ci, Co):
 
 # tcgen05 path: output widths 32/64/128, pixel counts that leave a partial 128-pixel tile,
 # K = 9*Cin that leaves a partial 64-element slice, batches that cross images in one tile
-@pytest.mark.parametrize("B,H,W,Ci,Co", [(1, 24, 24, 40, 128), (3, 10, 14, 8, 32), (2, 64, 64, 64, 64),
-                                         (1, 8, 16, 128, 128)])
+@pytest.mark.parametrize("B,H,W,Ci,Co", [(1, 24, 24, 40, 128), (3, 10, 14, 32, 32), (2, 64, 64, 64, 64),
+                                         (1, 8, 16, 128, 128), (3, 10, 14, 8, 32)])
 @pytest.mark.parametrize("legacy", [False, True])
 def test_conv_forward_tcgen05_and_legacy(cuda, B, H, W, Ci, Co, legacy):
     rng = np.random.default_rng(B * 1000 + H * 10 + Ci)
