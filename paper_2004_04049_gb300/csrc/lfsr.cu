@@ -15,7 +15,7 @@ namespace holo {
 
 constexpr uint32_t kLfsrLow = (1u << 3) | 1u;   // p(x) without its x^31 term
 constexpr uint32_t kLfsrMask = 0x7FFFFFFFu;
-constexpr int kLfsrRun = 512;
+constexpr int kLfsrRun = 512;   // codes per thread (a multiple of 16)
 
 __host__ __device__ __forceinline__ uint32_t lfsr_step(uint32_t s) {
     return ((s << 1) & kLfsrMask) ^ ((s >> 30) ? kLfsrLow : 0u);
@@ -35,7 +35,19 @@ __host__ __device__ __forceinline__ uint32_t lfsr_mulmod(uint32_t a, uint32_t b)
 
 __constant__ uint32_t c_xpow[64];   // x^(2^j) mod p
 
-__global__ void k_lfsr_codes(uint32_t s0, uint64_t start, int64_t count, int bits, uint8_t* __restrict__ codes) {
+__device__ __forceinline__ uint32_t lfsr_code(uint32_t& s, int bits) {
+    uint32_t c = 0;
+    for (int b = 0; b < bits; ++b) {
+        c = (c << 1) | (s >> 30);
+        s = lfsr_step(s);
+    }
+    return c;
+}
+
+// vec16: the output is 16-byte aligned, so full groups of 16 codes go out as one uint4
+// store (byte stores from threads 512 bytes apart would each cost a separate sector write)
+__global__ void k_lfsr_codes(uint32_t s0, uint64_t start, int64_t count, int bits, int vec16,
+                             uint8_t* __restrict__ codes) {
     pdl_wait();   // a previous kernel may still read the buffer being rewritten
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t c0 = t * kLfsrRun;
@@ -45,14 +57,21 @@ __global__ void k_lfsr_codes(uint32_t s0, uint64_t start, int64_t count, int bit
     for (int j = 0; j < 64 && k; ++j, k >>= 1)
         if (k & 1u) s = lfsr_mulmod(s, c_xpow[j]);
     const int64_t n = count - c0 < kLfsrRun ? count - c0 : kLfsrRun;
-    for (int64_t i = 0; i < n; ++i) {
-        uint32_t c = 0;
-        for (int b = 0; b < bits; ++b) {
-            c = (c << 1) | (s >> 30);
-            s = lfsr_step(s);
+    int64_t i = 0;
+    if (vec16) {
+        for (; i + 16 <= n; i += 16) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) v |= lfsr_code(s, bits) << (8 * b);
+                w[q] = v;
+            }
+            *reinterpret_cast<uint4*>(codes + c0 + i) = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        codes[c0 + i] = uint8_t(c);
     }
+    for (; i < n; ++i) codes[c0 + i] = uint8_t(lfsr_code(s, bits));
 }
 
 // fills the power table on the current device once
@@ -97,7 +116,8 @@ extern "C" int lfsr_build(uint32_t seed_state, int64_t start, int64_t count, int
     const int block = 128;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
     Launch ln("lfsr_build", st);
+    const int vec16 = (reinterpret_cast<uintptr_t>(d_codes) & 15) == 0;
     const cudaError_t le = launch_pdl(k_lfsr_codes, dim3(unsigned((threads + block - 1) / block)), dim3(block), 0, st,
-                                      seed_state, uint64_t(start), count, log2i(levels), d_codes);
+                                      seed_state, uint64_t(start), count, log2i(levels), vec16, d_codes);
     return ln.done("lfsr_build launch", le);
 }

@@ -25,6 +25,16 @@ def test_codes_bit_exact(cuda, seed, start, count, levels):
     assert np.array_equal(d.cpu().numpy().astype(np.int64), olfsr.codes(seed, start, count, levels))
 
 
+def test_codes_unaligned_output(cuda):
+    # an output pointer off a 16-byte boundary takes the byte-store path
+    d = torch.zeros(4100, dtype=torch.uint8, device=cuda)
+    holo.lfsr_build(321, 10, 4097, 256, d[3:])
+    torch.cuda.synchronize()
+    got = d.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got[3:3 + 4097], olfsr.codes(321, 10, 4097))
+    assert got[:3].sum() == 0
+
+
 def test_ospr_with_m_sequence_codes(cuda):
     H = W = 128
     N = 4
