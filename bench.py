@@ -790,7 +790,7 @@ def conv_throughput(reps=20):
             ms = e0.elapsed_time(e1) / reps
             row[kind] = {"us": ms * 1e3, "tflops": flops / (ms / 1e3) / 1e12}
         out[name] = row
-    out["tc_fault"] = holo.nn_tc_status()
+    out["tc_fault"] = holo.holo_tc_status()
     return out
 
 

@@ -410,12 +410,13 @@ int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, const void* d_i
                float* d_out_f32, float* d_dw, holo_stream_t s);
 
 /*
- * nn_tc_status - the tcgen05 convolution kernels bound every wait on their pipeline
- * barriers; a wait that expires makes the kernel skip its outputs, free its tensor memory
- * and set a device flag. Writes that flag to *fault (0 = never) and clears it when
- * `clear` is nonzero. Synchronous (reads device memory).
+ * holo_tc_status - the tcgen05 kernels (the convolutions, the DFT-32 stages of the
+ * tensor-core precisions) bound every wait on their mbarriers; a wait that expires sets a
+ * device flag (the convolution then skips its outputs; results of a DFT stage are not to
+ * be trusted). Writes whether any flag is set to *fault (0 = never) and clears the flags
+ * when `clear` is nonzero. Synchronous (reads device memory).
  */
-int nn_tc_status(int* fault, int clear);
+int holo_tc_status(int* fault, int clear);
 
 /* ------------------------------------------------------------ replay error ---- */
 

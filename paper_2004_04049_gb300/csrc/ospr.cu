@@ -277,6 +277,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
     a.tc = tab.tc[precision];
+    a.tc05b = tab.tc05b[precision];
     if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
     // Section 8 design rules: warnings only
     if (L > 0) {
@@ -503,6 +504,7 @@ extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
     a.N = N;
     a.ps = ps;
     a.tc = nullptr;
+    a.tc05b = nullptr;
     a.zbuf = static_cast<float2*>(scratch);
     a.sacc = reinterpret_cast<float*>(static_cast<char*>(scratch) + pl.z_bytes);
     a.groups = pl.groups;

@@ -81,6 +81,7 @@ struct OsprArgs {
     const float2* tw;
     const float2* cs256;
     const TcFrags* tc;    // DFT-32 A fragments of the tensor-core precision in use
+    const uint8_t* tc05b; // tcgen05 DFT-32 matrices of that precision ([direction][hi, lo])
 };
 
 template <int NC, int V>

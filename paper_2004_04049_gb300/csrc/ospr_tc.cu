@@ -1,8 +1,119 @@
 // ospr_tc.cu - launchers of the OSPR passes whose radix-32 DFT stages run on the tensor
 // cores (split fp16 or bf16 operands, float32 accumulation), for line lengths 1024 and 2048.
 #include "ospr_kernels.cuh"
+#include "tc05_dft.cuh"
 
 namespace holo {
+
+// ---------------------------------------------------------------- tcgen05 ----
+// Column DFT + accumulate pass (k_ospr_col_fft) for 1024-point columns with both radix-32
+// stages on tcgen05 (tc05_dft.cuh). Tile: 8 columns x 32 threads = 256 threads, i.e. two
+// MMA groups of 128 sub-lines. Shared memory: the DFT matrix (hi, lo) for the forward
+// direction of this pass, then the padded line buffers, whose first 64 KiB also hold the
+// groups' A tiles, then two mbarriers.
+static __device__ int g_tc05_dft_fault;
+
+constexpr int kTc05Lpc = ColCfg<1024, 1>::LPC;
+constexpr int kTc05Threads = (1024 / 32) * kTc05Lpc;
+constexpr size_t kTc05LineBytes = sizeof(float2) * kTc05Lpc * col_stride<1024, 1>();
+constexpr size_t kTc05Smem = 1024 + 2 * kTc05BBytes + kTc05LineBytes + 16;
+static_assert(kTc05Threads == 256 && 2 * 2 * kTc05TileBytes <= kTc05LineBytes, "tcgen05 column tile");
+
+template <int PREC>
+__global__ void __launch_bounds__(kTc05Threads, 2) k_ospr_col_fft_tc05(OsprArgs a) {
+    constexpr int NC = 1024, R = 32, LPC = kTc05Lpc, T = NC / R, S = col_stride<1024, 1>();
+    extern __shared__ uint8_t smraw[];
+    __shared__ uint32_t s_tmem;
+    const uint32_t raw = static_cast<uint32_t>(__cvta_generic_to_shared(smraw));
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* const sm = smraw + (base - raw);
+    float2* lines = reinterpret_cast<float2*>(sm + 2 * kTc05BBytes);
+    const uint32_t lines_u32 = base + 2 * kTc05BBytes;
+    const uint32_t bar0 = lines_u32 + uint32_t(kTc05LineBytes);
+    const int tid = threadIdx.x;
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(&s_tmem)))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8) : "memory");
+    }
+    // the inverse-direction matrix: direction index 0 (-1) of this precision's table
+    const uint4* bsrc = reinterpret_cast<const uint4*>(a.tc05b);
+    uint4* bdst = reinterpret_cast<uint4*>(sm);
+    for (int i = tid; i < 2 * kTc05BBytes / 16; i += kTc05Threads) bdst[i] = __ldg(bsrc + i);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+    Tc05Group g;
+    const int grp = tid >> 7;
+    g.row = tid & 127;
+    g.a_hi = lines_u32 + uint32_t(grp) * 2u * kTc05TileBytes;
+    g.a_lo = g.a_hi + kTc05TileBytes;
+    g.b_hi = base;
+    g.b_lo = base + kTc05BBytes;
+    g.bar = bar0 + 8u * grp;
+    g.tmem = s_tmem + 64u * grp;
+    g.phase = 0;
+    g.fault = &g_tc05_dft_fault;
+
+    const int lc = tid % LPC, t = tid / LPC;
+    const int W = a.W;
+    const int c = blockIdx.x * LPC + lc;
+    const size_t P = size_t(NC) * W;
+    pdl_wait();
+    float acc[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) acc[e] = 0.f;
+    for (int j = blockIdx.y; j < a.pairs; j += a.groups) {
+        const float2* z = a.zbuf + size_t(j) * P;
+        float2 v[R];
+#pragma unroll
+        for (int e = 0; e < R; ++e) v[e] = z[size_t(t + T * e) * W + c];
+        line_fft_1024_tc05<-1, PREC>(v, lines + lc * S, t, a.tw, g);
+#pragma unroll
+        for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
+    }
+    pdl_trigger();
+    float* Sacc = a.sacc + size_t(blockIdx.y) * P;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const size_t i = size_t(t + T * e) * W + c;
+        Sacc[i] = a.accumulate ? Sacc[i] + acc[e] : acc[e];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if ((tid >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(s_tmem) : "memory");
+}
+
+template <int PREC>
+static int launch_col_fft_tc05(const OsprArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    int rc = ensure_smem((const void*)k_ospr_col_fft_tc05<PREC>, kTc05Smem, &mask);
+    if (rc) return rc;
+    dim3 grid(a.W / kTc05Lpc, a.groups);
+    Launch ln("ospr_col_fft", st);
+    const cudaError_t le = launch_pdl(k_ospr_col_fft_tc05<PREC>, grid, dim3(kTc05Threads), kTc05Smem, st, a);
+    return ln.done("ospr_col_fft tcgen05 launch", le);
+}
+
+int ospr_tc05_fault(int* out, bool clear) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc05_dft_fault, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e, "ospr_tc05_fault");
+    if (clear && v) {
+        const int z = 0;
+        if ((e = cudaMemcpyToSymbol(g_tc05_dft_fault, &z, sizeof(int))) != cudaSuccess)
+            return cuda_status(e, "ospr_tc05_fault");
+    }
+    *out = v;
+    return HOLO_OK;
+}
 
 template <int NC, int PREC>
 static int launch_col_ifft_tc(const OsprArgs& a, cudaStream_t st) {
@@ -49,7 +160,7 @@ int ospr_run_col_ifft_tc(const OsprArgs& a, int prec, cudaStream_t st) {
     return fail(HOLO_EUNSUPPORTED, "tensor-core stages: column length %d", a.H);
 }
 int ospr_run_col_fft_tc(const OsprArgs& a, int prec, cudaStream_t st) {
-    if (a.H == 1024) return prec == kTcBf16 ? launch_col_fft_tc<1024, kTcBf16>(a, st) : launch_col_fft_tc<1024, kTcFp16>(a, st);
+    if (a.H == 1024) return prec == kTcBf16 ? launch_col_fft_tc05<kTcBf16>(a, st) : launch_col_fft_tc05<kTcFp16>(a, st);
     if (a.H == 2048) return prec == kTcBf16 ? launch_col_fft_tc<2048, kTcBf16>(a, st) : launch_col_fft_tc<2048, kTcFp16>(a, st);
     return fail(HOLO_EUNSUPPORTED, "tensor-core stages: column length %d", a.H);
 }

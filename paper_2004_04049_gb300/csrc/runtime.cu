@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fft_core.cuh"
+#include "tc05_dft.cuh"
 #include "tc_dft.cuh"
 
 namespace holo {
@@ -164,6 +165,48 @@ static void host_tc_frags(TcFrags* out, bool bf16) {
             }
 }
 
+// tcgen05 DFT-32 B operands: [precision fp16, bf16][direction -1, +1][hi, lo][8192 bytes].
+// Row j (output) holds the coefficients of input i (K): outputs 0..31 are Re X_k, 32..63
+// Im X_k; inputs 0..31 are Re x_n, 32..63 Im x_n; X_k = sum_n x_n exp(i DIR 2 pi n k / 32).
+static __device__ uint4 g_tc05_b[2 * 2 * 2 * 8192 / 16];
+
+static void host_tc05_b(uint8_t* out, bool bf16) {
+    const double two_pi = 6.283185307179586476925286766559;
+    auto conv = [&](float x) -> uint16_t {
+        if (bf16) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(x);
+            return *reinterpret_cast<const uint16_t*>(&b);
+        }
+        const __half h = __float2half_rn(x);
+        return *reinterpret_cast<const uint16_t*>(&h);
+    };
+    auto back = [&](uint16_t u) -> float {
+        if (bf16) return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(&u));
+        return __half2float(*reinterpret_cast<const __half*>(&u));
+    };
+    for (int d = 0; d < 2; ++d) {
+        const double dir = d == 0 ? -1.0 : 1.0;
+        uint8_t* hi = out + size_t(d) * 2 * 8192;
+        uint8_t* lo = hi + 8192;
+        for (int j = 0; j < 64; ++j)
+            for (int i = 0; i < 64; ++i) {
+                const int k = j & 31, n = i & 31;
+                const double ang = two_pi * double(n) * double(k) / 32.0;
+                double c;
+                if (j < 32 && i < 32) c = std::cos(ang);
+                else if (j < 32) c = -dir * std::sin(ang);
+                else if (i < 32) c = dir * std::sin(ang);
+                else c = std::cos(ang);
+                const float x = float(c);
+                const uint16_t h = conv(x);
+                const uint16_t l = conv(x - back(h));
+                const uint32_t off = sw128_offset(j, i);
+                memcpy(hi + off, &h, 2);
+                memcpy(lo + off, &l, 2);
+            }
+    }
+}
+
 static std::mutex g_tab_mu;
 static const int kMaxDevices = 64;
 static Tables g_tables[kMaxDevices];
@@ -209,6 +252,11 @@ int device_tables(Tables* out) {
         host_tc_frags(&fr[1], true);
         e = cudaMemcpyToSymbol(g_tc_frags, fr.data(), sizeof(TcFrags) * 2);
         if (e != cudaSuccess) return cuda_status(e, "upload tensor-core fragments");
+        std::vector<uint8_t> b05(sizeof(g_tc05_b));
+        host_tc05_b(b05.data(), false);
+        host_tc05_b(b05.data() + b05.size() / 2, true);
+        e = cudaMemcpyToSymbol(g_tc05_b, b05.data(), b05.size());
+        if (e != cudaSuccess) return cuda_status(e, "upload tcgen05 DFT matrices");
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_twiddles);
         if (e != cudaSuccess) return cuda_status(e, "twiddle address");
@@ -221,6 +269,11 @@ int device_tables(Tables* out) {
         g_tables[dev].tc[0] = nullptr;
         g_tables[dev].tc[1] = static_cast<const TcFrags*>(p);
         g_tables[dev].tc[2] = static_cast<const TcFrags*>(p) + 1;
+        e = cudaGetSymbolAddress(&p, g_tc05_b);
+        if (e != cudaSuccess) return cuda_status(e, "tcgen05 DFT matrix address");
+        g_tables[dev].tc05b[0] = nullptr;
+        g_tables[dev].tc05b[1] = static_cast<const uint8_t*>(p);
+        g_tables[dev].tc05b[2] = static_cast<const uint8_t*>(p) + 4 * 8192;
         g_tables_ready[dev] = true;
     }
     *out = g_tables[dev];

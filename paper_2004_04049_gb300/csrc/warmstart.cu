@@ -540,8 +540,17 @@ extern "C" int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, cons
     return conv3x3(a, mode, reinterpret_cast<cudaStream_t>(s), legacy);
 }
 
-extern "C" int nn_tc_status(int* fault, int clear) {
+namespace holo {
+int ospr_tc05_fault(int* out, bool clear);
+}
+
+extern "C" int holo_tc_status(int* fault, int clear) {
     clear_error();
-    if (!fault) return fail(HOLO_EINVAL, "nn_tc_status: NULL output");
-    return conv3x3_tc05_fault(fault, clear != 0);
+    if (!fault) return fail(HOLO_EINVAL, "holo_tc_status: NULL output");
+    int a = 0, b = 0;
+    int rc = conv3x3_tc05_fault(&a, clear != 0);
+    if (rc) return rc;
+    if ((rc = holo::ospr_tc05_fault(&b, clear != 0))) return rc;
+    *fault = a | b;
+    return HOLO_OK;
 }

@@ -109,7 +109,7 @@ _SIGS = {
     "nn_conv3x3": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.c_void_p,
                               _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p,
                               _c.c_void_p, _c.c_void_p]),
-    "nn_tc_status": (_c.c_int, [_c.POINTER(_c.c_int), _c.c_int]),
+    "holo_tc_status": (_c.c_int, [_c.POINTER(_c.c_int), _c.c_int]),
     "replay_error_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "replay_error": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int,
                                 _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
@@ -428,8 +428,8 @@ def nn_conv3x3(mode, B, H, W, Cin, Cout, d_in, d_wmat=None, d_dy=None, d_bias=No
 HOLO_CONV_LEGACY = 16
 
 
-def nn_tc_status(clear=False):
-    """1 if a tcgen05 convolution kernel gave up on a bounded wait since the last clear."""
+def holo_tc_status(clear=False):
+    """1 if a tcgen05 kernel gave up on a bounded wait since the last clear."""
     v = ctypes.c_int(0)
-    _call("nn_tc_status", ctypes.byref(v), 1 if clear else 0)
+    _call("holo_tc_status", ctypes.byref(v), 1 if clear else 0)
     return v.value

@@ -54,12 +54,12 @@ def test_conv_forward_tcgen05_and_legacy(cuda, B, H, W, Ci, Co, legacy):
     out = torch.zeros((B, H, W, Co), dtype=torch.float32, device=cuda)
     outb = torch.zeros((B, H, W, Co), dtype=torch.bfloat16, device=cuda)
     mode = holo.HOLO_CONV_LEGACY if legacy else 0
-    holo.nn_tc_status(clear=True)
+    holo.holo_tc_status(clear=True)
     holo.nn_conv3x3(mode, B, H, W, Ci, Co, _dev_bf16(x, cuda), _dev_bf16(w.reshape(Co, -1), cuda),
                     d_bias=torch.from_numpy(b).to(cuda), d_residual=_dev_bf16(res, cuda), relu=True,
                     d_out=outb, d_out_f32=out)
     torch.cuda.synchronize()
-    assert holo.nn_tc_status() == 0
+    assert holo.holo_tc_status() == 0
     ref = np.maximum(oc.conv3x3(x, w, b) + res, 0.0)
     g = out.cpu().numpy()
     assert np.max(np.abs(g - ref)) <= 1e-5 * max(1.0, np.abs(ref).max())

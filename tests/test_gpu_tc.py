@@ -35,6 +35,7 @@ def test_tc_parity(cuda, prec, H, W, N, kind):
     T = blob_target(H, W, 1300) if kind == "blob" else noise_target(H, W, 2300)
     t = torch.from_numpy(T).to(cuda)
     codes = pipeline.lut(seed, L, device=cuda)
+    holo.holo_tc_status(clear=True)
     bits, I = pipeline.ospr(t, N, codes, L, 256, seed, precision=prec)
     b32, I32 = pipeline.ospr(t, N, codes, L, 256, seed)
     err = pipeline.error(I, t)
@@ -52,6 +53,7 @@ def test_tc_parity(cuda, prec, H, W, N, kind):
     print(f"prec={prec} {H}x{W} N={N}: bits agree {agree:.7f} (vs fp32 path {vs32:.7f}), "
           f"replay rel {rel:.2e}, nmse rel vs oracle {nmse_rel:.2e}")
     assert vs32 >= 0.9999
+    assert holo.holo_tc_status() == 0
 
 
 def test_tc_rejects_other_shapes(cuda):
