@@ -880,6 +880,16 @@ def run_case(name):
             pipeline.gs(T, 2, 256, codes, GS_L, 256, LUT_SEED)
         torch.cuda.synchronize()
         print("case frame ok, nmse", float(e[2]))
+    elif name == "tc":
+        # one 1024x1024 frame (N=24, L=10007) twice in float32, then twice in bf16x2
+        from paper_2004_04049_gb300 import holo
+        T = torch.from_numpy(blob_target(H, W, 1000)).to(dev)
+        codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
+        for prec in (holo.HOLO_FP32, holo.HOLO_BF16X2):
+            for _ in range(2):
+                pipeline.ospr(T, N_SF, codes, GS_L, 256, LUT_SEED, precision=prec)
+        torch.cuda.synchronize()
+        print("case tc ok, tcgen05 fault flag", holo.holo_tc_status())
     else:
         raise SystemExit(f"unknown case {name!r}")
 
