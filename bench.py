@@ -880,6 +880,14 @@ def run_case(name):
             pipeline.gs(T, 2, 256, codes, GS_L, 256, LUT_SEED)
         torch.cuda.synchronize()
         print("case frame ok, nmse", float(e[2]))
+    elif name == "gs":
+        # GS at 1024x1024: 20 iterations from the LUT-random start, default tiles, twice
+        T = torch.from_numpy(blob_target(H, W, 1000)).to(dev)
+        codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
+        for _ in range(2):
+            out = pipeline.gs(T, GS_ITERS, 256, codes, GS_L, 256, LUT_SEED)
+        torch.cuda.synchronize()
+        print("case gs ok, eps_20 / P", float(out["err"][-1]) / (H * W))
     elif name == "tc":
         # one 1024x1024 frame (N=24, L=10007) twice in float32, then twice in bf16x2
         from paper_2004_04049_gb300 import holo

@@ -190,3 +190,28 @@ def test_full_size_1024_sampled(cuda):
         assert abs(gI[u, v] - Iuv) <= 1e-4 * gI.max(), (u, v, gI[u, v], Iuv)
     o_stage = oerr.replay_error(gI, T)
     check_nmse(gerr[2], o_stage[2])
+
+
+def test_largest_size_4096(cuda):
+    """The largest supported shape (4096x4096, N = 2): sub-frame 0 element by element, the
+    replay's symmetry and unitarity, and sampled replay pixels by direct DFT sums of the
+    GPU's bits."""
+    H = W = 4096
+    N, L, seed = 2, 10007, 3
+    P = H * W
+    T = blob_target(H, W, 1010)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, L, seed)
+    table = olut.lut_codes(seed, L)
+    c = olut.subframe_codes(table, L, seed, 0, 0, P, P)
+    Hs = oospr.back_propagate(oospr.subframe_field(T, c))
+    check_bits(gb[0:1], oospr.pack_bits(oospr.binarise(Hs.real))[None, :], [Hs.real], P)
+    twin = np.roll(np.flip(gI), shift=(1, 1), axis=(0, 1))
+    assert np.array_equal(gI, twin)
+    assert abs(gI.sum() / P - 1.0) < 1e-4
+    hs = np.where(unpack(gb, P), -1.0, 1.0).reshape(N, H, W)
+    r = np.arange(H)[:, None]
+    cc = np.arange(W)[None, :]
+    for (u, v) in [(0, 0), (H // 2, 17), (123, 3999)]:
+        ph = np.exp(-2j * np.pi * (u * r / H + v * cc / W))
+        R = np.tensordot(hs, ph, axes=([1, 2], [0, 1])) / np.sqrt(P)
+        assert abs(gI[u, v] - np.mean(np.abs(R) ** 2)) <= 1e-4 * gI.max()
