@@ -6,13 +6,13 @@
 // eps = sum (|R| - T_s)^2; E = T_s exp(i arg R).
 //
 // Passes (one global round trip of the complex field each; the field stays resident):
-//   prepare    sum T^2 -> scale (float64 grid reduction)
+//   prepare    sum T^2 -> scale (float-float block partials, ffloat.cuh)
 //   col_init   columns: E_0 from the LUT / a phase / a saved state, column IDFT
 //   row        rows: row IDFT, quantise (codes out on the last iteration), row DFT
 //   col        columns: column DFT, error partials, amplitude constraint, column IDFT
 //              (the next iteration's first half); on the last iteration it writes
 //              |R|^2 and the state instead of transforming back
-//   finish     per-iteration float64 error sums
+//   finish     per-iteration error sums (float-float, converted to float64 once)
 #include <cmath>
 #include <cstdlib>
 #include <map>
