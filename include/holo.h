@@ -418,6 +418,15 @@ int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, const void* d_i
  */
 int holo_tc_status(int* fault, int clear);
 
+/*
+ * holo_wait_selftest - exercises the bounded-wait path of the tcgen05 kernels without a
+ * fault: one warp waits on an mbarrier that nothing arrives at, gives up after `limit`
+ * polls (1 .. 2^24) and sets the same device flag a real expiry sets. Synchronises s.
+ * Returns HOLO_ETIMEOUT (the expected result) with the flag set; holo_check then reports
+ * HOLO_ETIMEOUT too until holo_tc_status clears the flag. The context stays usable.
+ */
+int holo_wait_selftest(int limit, holo_stream_t s);
+
 /* ------------------------------------------------------------ replay error ---- */
 
 /*

@@ -102,6 +102,17 @@ static int launch_col_fft_tc05(const OsprArgs& a, cudaStream_t st) {
     return ln.done("ospr_col_fft tcgen05 launch", le);
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing arrives at,
+// gives up after `limit` polls and records the fault exactly as the tcgen05 kernels do.
+__global__ void k_wait_selftest(uint32_t limit) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+    __syncwarp();
+    const bool done = tc05_wait(b, 0u, limit);
+    if (!done && threadIdx.x == 0) atomicExch(&g_tc05_dft_fault, 1);
+}
+
 int ospr_tc05_fault(int* out, bool clear) {
     int v = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc05_dft_fault, sizeof(int));
@@ -177,3 +188,19 @@ int ospr_run_row_tc(const OsprArgs& a, int prec, bool replay, cudaStream_t st) {
 }
 
 }  // namespace holo
+
+using namespace holo;
+
+extern "C" int holo_wait_selftest(int limit, holo_stream_t s) {
+    clear_error();
+    if (limit < 1 || limit > (1 << 24)) return fail(HOLO_EINVAL, "holo_wait_selftest: limit %d out of [1, 2^24]", limit);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    Launch ln("wait_selftest", st);
+    k_wait_selftest<<<1, 32, 0, st>>>(uint32_t(limit));
+    int rc = ln.done("wait_selftest launch");
+    if (rc) return rc;
+    if ((rc = cuda_status(cudaStreamSynchronize(st), "holo_wait_selftest"))) return rc;
+    int f = 0;
+    if ((rc = ospr_tc05_fault(&f, false))) return rc;
+    return f ? fail(HOLO_ETIMEOUT, "holo_wait_selftest: the wait gave up after %d polls", limit) : HOLO_OK;
+}

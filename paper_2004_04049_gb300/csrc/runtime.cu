@@ -308,6 +308,10 @@ extern "C" int holo_check(holo_stream_t s) {
     if (e != cudaSuccess) return cuda_status(e, "holo_check: stream");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "holo_check");
+    int fault = 0;
+    int rc = holo_tc_status(&fault, 0);
+    if (rc) return rc;
+    if (fault) return fail(HOLO_ETIMEOUT, "holo_check: a tcgen05 kernel gave up on a bounded wait");
     return HOLO_OK;
 }
 

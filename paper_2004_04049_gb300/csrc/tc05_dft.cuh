@@ -76,8 +76,10 @@ __device__ __forceinline__ void tc05_sts128(uint32_t addr, uint32_t a, uint32_t 
                  : "memory");
 }
 
-__device__ __forceinline__ bool tc05_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kTc05WaitLimit; ++i) {
+// true once the mbarrier phase of the given parity has completed; false after `limit`
+// polls (the caller then records a fault instead of waiting on)
+__device__ __forceinline__ bool tc05_wait(uint32_t bar, uint32_t parity, uint32_t limit = kTc05WaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

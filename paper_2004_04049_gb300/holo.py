@@ -110,6 +110,7 @@ _SIGS = {
                               _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_void_p, _c.c_void_p,
                               _c.c_void_p, _c.c_void_p]),
     "holo_tc_status": (_c.c_int, [_c.POINTER(_c.c_int), _c.c_int]),
+    "holo_wait_selftest": (_c.c_int, [_c.c_int, _c.c_void_p]),
     "replay_error_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "replay_error": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int,
                                 _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
@@ -433,3 +434,12 @@ def holo_tc_status(clear=False):
     v = ctypes.c_int(0)
     _call("holo_tc_status", ctypes.byref(v), 1 if clear else 0)
     return v.value
+
+
+def holo_wait_selftest(limit=1000, stream=None):
+    """Raw status of the bounded-wait self-test (HOLO_ETIMEOUT is the expected result)."""
+    s = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else None)
+    if s is None:
+        import torch
+        s = torch.cuda.current_stream().cuda_stream
+    return load().holo_wait_selftest(limit, s)

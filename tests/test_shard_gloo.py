@@ -66,3 +66,40 @@ def test_two_rank_subframe_split(tmp_path):
         assert np.max(np.abs(I - I_ref)) <= 1e-12 * I_ref.max()
         first, count = np.load(tmp_path / f"first_{r}.npy")
         assert np.array_equal(np.load(tmp_path / f"bits_{r}.npy"), bits_ref[first:first + count])
+
+
+def _failing_worker(rank, world, port, out_dir):
+    """Rank 1 fails before the frame's sum-reduction (it raises, as a crashed rank would);
+    rank 0 must learn of it from the collective, within the process group's timeout,
+    instead of waiting forever."""
+    import datetime
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        raise RuntimeError("rank 1 fails before the reduction")
+    T = blob_target(H, W, 1000)
+    table = olut.lut_codes(SEED, L)
+    first, count, start = shard.subframe_shard(N, 0, H * W, rank, world)
+    _, I, _ = oospr.ospr(T, count, table, L, SEED, start=start, stride=H * W)
+    part = torch.from_numpy(I * count)
+    try:
+        dist.all_reduce(part, op=dist.ReduceOp.SUM)
+        outcome = "completed"
+    except RuntimeError as e:
+        outcome = "detected: " + str(e).splitlines()[0][:200]
+    with open(os.path.join(out_dir, "rank0.txt"), "w") as f:
+        f.write(outcome)
+
+
+def test_failed_rank_is_detected(tmp_path):
+    world = 2
+    ctx = mp.start_processes(_failing_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                             join=False, start_method="spawn")
+    for p in ctx.processes:
+        p.join(120)
+    codes = {i: p.exitcode for i, p in enumerate(ctx.processes)}
+    assert codes[1] not in (0, None)                 # the failing rank exits with an error
+    assert codes[0] == 0                             # the survivor returns, it does not hang
+    assert (tmp_path / "rank0.txt").read_text().startswith("detected")
