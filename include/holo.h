@@ -65,7 +65,11 @@ int holo_version(void);
 const char* holo_last_error(void);
 
 /* Synchronises stream s and reports any CUDA error raised by earlier calls, and the
- * library's sticky device status (HOLO_ETIMEOUT if a bounded wait gave up). */
+ * library's sticky device status (HOLO_ETIMEOUT if a bounded wait gave up).
+ * Host-side fault injection for tests: the environment variable HOLO_FAULT_INJECT, a
+ * comma-separated list, makes "timeout" holo_check return HOLO_ETIMEOUT, "alloc"
+ * ospr_autotune's scratch allocation fail (HOLO_ENOMEM) and "plan" batch planning fail
+ * (HOLO_EINVAL), before any device work. */
 int holo_check(holo_stream_t s);
 
 /* Number of kernels this library has launched in this process (all devices). */

@@ -70,6 +70,7 @@ struct BatchPlan {
 
 static int plan_batch(const holo_frame_desc* f, int n, int precision, BatchPlan* pl) {
     if (!f || n < 1) return fail(HOLO_EINVAL, "batch: no frames");
+    if (fault_injected("plan")) return fail(HOLO_EINVAL, "batch: injected planning failure (HOLO_FAULT_INJECT)");
     size_t max_ospr = 0, max_err = 0;
     std::vector<double> cost(n);
     for (int i = 0; i < n; ++i) {

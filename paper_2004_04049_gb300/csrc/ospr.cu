@@ -330,6 +330,7 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
     const int64_t L = 10007;
     // the largest candidate plan bounds the workspace
     const size_t ws_bytes = ospr_plan_with(H, W, N, OsprTuning{0, 0, 0, kMaxChunkPairs, kMaxGroups}).total;
+    if (fault_injected("alloc")) return fail(HOLO_ENOMEM, "%s: injected allocation failure (HOLO_FAULT_INJECT)", who);
     void *d_t = nullptr, *d_codes = nullptr, *d_bits = nullptr, *d_rep = nullptr, *d_ws = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaMalloc(&d_t, P * sizeof(float));

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -102,6 +103,20 @@ int Launch::done(const char* what, cudaError_t launch) {
 }
 
 int profiling_swap(int on) { return g_profiling.exchange(on ? 1 : 0); }
+
+bool fault_injected(const char* kind) {
+    const char* v = getenv("HOLO_FAULT_INJECT");
+    if (!v || !*v) return false;
+    const size_t n = strlen(kind);
+    for (const char* p = v; *p;) {
+        const char* e = strchr(p, ',');
+        const size_t len = e ? size_t(e - p) : strlen(p);
+        if (len == n && strncmp(p, kind, n) == 0) return true;
+        if (!e) break;
+        p = e + 1;
+    }
+    return false;
+}
 
 static int collect_locked() {
     for (auto& kv : g_prof) {
@@ -304,6 +319,7 @@ extern "C" const char* holo_last_error(void) { return t_last_error.c_str(); }
 
 extern "C" int holo_check(holo_stream_t s) {
     clear_error();
+    if (fault_injected("timeout")) return fail(HOLO_ETIMEOUT, "holo_check: injected timeout (HOLO_FAULT_INJECT)");
     cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s));
     if (e != cudaSuccess) return cuda_status(e, "holo_check: stream");
     e = cudaGetLastError();

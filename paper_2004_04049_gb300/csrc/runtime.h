@@ -38,6 +38,11 @@ class Launch {
 // Sets event profiling on or off and returns the previous setting.
 int profiling_swap(int on);
 
+// Host-side fault injection for tests: true when the environment variable
+// HOLO_FAULT_INJECT (a comma-separated list) names `kind` ("alloc": scratch allocations
+// fail, "timeout": holo_check reports an expired wait, "plan": batch planning fails).
+bool fault_injected(const char* kind);
+
 // ---- programmatic dependent launch ------------------------------------------------
 // A kernel launched with launch_pdl may be scheduled while the previous kernel on its
 // stream is still running, which hides the launch latency between dependent kernels.

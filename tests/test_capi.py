@@ -136,3 +136,17 @@ def test_lfsr_build_validation_host_only(lib):
         assert ei.value.status == holo.HOLO_EINVAL
     with pytest.raises(holo.HoloError):
         holo.lfsr_build(1, 0, 16, 256, None)
+
+
+def test_host_fault_injection(lib, monkeypatch):
+    monkeypatch.setenv("HOLO_FAULT_INJECT", "plan,timeout,alloc")
+    assert lib.holo_check(None) == holo.HOLO_ETIMEOUT
+    assert "injected" in holo.last_error()
+    v = ctypes.c_double(0.0)
+    assert lib.ospr_autotune(256, 256, 4, 1, None, ctypes.byref(v)) == holo.HOLO_ENOMEM
+    arr = holo.frame_array([holo.frame_desc(1 << 20, 512, 512, 9, None, 0, 256, 0, False, 0, 0, 1 << 22, None, None)])
+    with pytest.raises(holo.HoloError) as ei:
+        holo.ospr_batch_workspace_size(arr)
+    assert ei.value.status == holo.HOLO_EINVAL and "injected" in str(ei.value)
+    monkeypatch.setenv("HOLO_FAULT_INJECT", "allocx")
+    assert holo.ospr_batch_workspace_size(arr) > 0
