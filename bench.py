@@ -847,7 +847,8 @@ def run_learned(args):
     holo.load()
     conv = conv_throughput()
     res = warmstart.run(n_train=args.learned_n, gs_iters=100, epochs=args.learned_epochs, batch=16,
-                        eval_size=1024, n_eval=8, log=lambda s: print(s, file=sys.stderr))
+                        eval_size=1024, n_eval=8, log=lambda s: print(s, file=sys.stderr),
+                        extra_sizes=(2048, 4096))
     peaks = _peaks()
     ev = res["eval"]
     line = {"metric": "learned GS warm start: GS iterations to the 20-iteration LUT-random error at 1024^2",
@@ -858,6 +859,12 @@ def run_learned(args):
             "ms_lut_mean": float(np.mean([r["ms_lut"] for r in ev])),
             "ms_learned_mean": float(np.mean([r["ms_learned"] or np.nan for r in ev])),
             "eval": ev, "seconds": res["seconds"], "conv_kernel": conv,
+            "other_sizes": {S: {"iters_lut_mean": float(np.mean([r["iters_lut"] for r in rows])),
+                                "iters_learned_mean": float(np.mean([r["iters_learned"] or 60 for r in rows])),
+                                "ms_lut_mean": float(np.mean([r["ms_lut"] for r in rows])),
+                                "ms_learned_mean": float(np.mean([r["ms_learned"] or np.nan for r in rows])),
+                                "eval": rows}
+                            for S, rows in res["eval_other_sizes"].items()},
             "bf16_peak_tflops": peaks["bf16_tflops"] if peaks else 1900.0}
     print(json.dumps(line), flush=True)
 

@@ -93,9 +93,10 @@ template <int NC, int V>
 constexpr size_t gs_col_smem() {
     return sizeof(float2) * (256 + size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>());
 }
+// the row pass looks up the quantised codes in a 16-way replicated table (conflict-free)
 template <int NR, int V>
 constexpr size_t gs_row_smem() {
-    return sizeof(float2) * (256 + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
+    return sizeof(float2) * (kCsSmemEntries + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
 }
 
 // ----------------------------------------------------------------- prepare ----
@@ -170,8 +171,8 @@ k_gs_row(GsArgs a) {
     constexpr bool BLOCK = T > 32;
     extern __shared__ float2 sm[];
     float2* cs = sm;
-    float2* lines = sm + 256;
-    load_cs_table<1>(cs, a.cs256);
+    float2* lines = sm + kCsSmemEntries;
+    load_cs_table(cs, a.cs256);
     pdl_wait();
     __syncthreads();
     const int line = threadIdx.x / T, t = threadIdx.x % T;
@@ -190,7 +191,7 @@ k_gs_row(GsArgs a) {
         const float ang = atan2f(v[e].y, v[e].x);
         const int q = int(floorf(fmaf(ang, k_code, 0.5f))) & (levels - 1);
         if (a.codes_out) a.codes_out[size_t(r) * NR + t + T * e] = uint8_t(q);
-        v[e] = cs_lookup<1>(cs, uint32_t(q) << shift);
+        v[e] = cs_lookup(cs, uint32_t(q) << shift);
     }
     line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
     pdl_trigger();
@@ -200,7 +201,8 @@ k_gs_row(GsArgs a) {
 
 // -------------------------------------------------------------------- col ----
 template <int NC, int V, bool LAST>
-__global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC)
+__global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC,
+                                  (NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC <= 256 ? 2 : 1)
 k_gs_col(GsArgs a) {
     constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
     extern __shared__ float2 sm[];
@@ -211,18 +213,25 @@ k_gs_col(GsArgs a) {
     const int c = blockIdx.x * LPC + lc;
     float2* buf = lines + lc * gs_col_stride<NC, V>();
     pdl_wait();
+    // the target and the scale do not depend on the transform: load them with the field
+    // so that their latency hides behind the column DFT
+    const size_t rs = size_t(T) * W;                 // element stride of a thread's slots
+    const size_t p0 = size_t(t) * W + c;
+    float tg[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) tg[e] = __ldg(a.target + p0 + e * rs);
+    const float scale = a.sc->scale;
     float2 v[R];
 #pragma unroll
-    for (int e = 0; e < R; ++e) v[e] = a.y[size_t(t + T * e) * W + c];
+    for (int e = 0; e < R; ++e) v[e] = a.y[p0 + e * rs];
     line_fft<NC, R, -1, true>(v, buf, t, a.tw);
-    const float scale = a.sc->scale;
     float err = 0.f;
 #pragma unroll
     for (int e = 0; e < R; ++e) {
-        const size_t p = size_t(t + T * e) * W + c;
+        const size_t p = p0 + e * rs;
         const float2 Rv = make_float2(v[e].x * a.inv_sqrt_p, v[e].y * a.inv_sqrt_p);
         const float amp = sqrtf(fmaf(Rv.x, Rv.x, Rv.y * Rv.y));
-        const float ts = __ldg(a.target + p) * scale;
+        const float ts = tg[e] * scale;
         const float d = amp - ts;
         err = fmaf(d, d, err);
         float2 En = make_float2(ts, 0.f);
@@ -258,8 +267,8 @@ k_gs_finish(const ff* __restrict__ err_part, int nb, double* __restrict__ err) {
 
 // ------------------------------------------------------------------- host ----
 // Tile variants per shape. Defaults (GB300, 20 iterations, CUDA events): 1024^2 takes
-// column variant 0 and row variant 1 (20.5 us per iteration against 24.5 for 0/0),
-// 2048^2 column 1 and row 1 (75 against 106 us).
+// column variant 0 and row variant 1 (19.9 us per iteration against 22.4 for 0/0),
+// 2048^2 column 1 and row 2 (71.9 against 85.7 us).
 struct GsTiles {
     int col_v, row_v;
 };
@@ -274,7 +283,7 @@ static GsTiles gs_tiles(int H, int W) {
     }
     GsTiles t;
     t.col_v = H == 2048 ? 1 : 0;
-    t.row_v = (W == 1024 || W == 2048) ? 1 : 0;
+    t.row_v = W == 1024 ? 1 : (W == 2048 ? 2 : 0);
     return t;
 }
 

@@ -113,9 +113,11 @@ def evaluate(net, targets, iters=60, ref_iter=20, stream=None):
 
 
 def run(n_train=20000, gs_iters=100, epochs=2, batch=16, lr=1e-3, n_eval=8, eval_size=1024, seed=5,
-        device="cuda", log=print):
+        device="cuda", log=print, extra_sizes=()):
     """The whole pipeline: seeded targets (half blobs, half band-limited noise), labels from
-    GS, training, evaluation at eval_size (the 256^2 prediction upsampled)."""
+    GS, training, evaluation at eval_size (the 256^2 prediction upsampled); `extra_sizes`
+    repeats the evaluation with 4 targets at other sizes (a larger field makes each saved
+    GS iteration worth more against the fixed inference cost)."""
     from synthetic import blob_target, noise_target
 
     dev = torch.device(device)
@@ -136,7 +138,13 @@ def run(n_train=20000, gs_iters=100, epochs=2, batch=16, lr=1e-3, n_eval=8, eval
         ev = [torch.from_numpy(blob_target(eval_size, eval_size, 900000 + i) if i % 2 == 0
                                else noise_target(eval_size, eval_size, 900000 + i)).to(dev) for i in range(n_eval)]
         rows = evaluate(net, ev)
+        extra = {}
+        for S in extra_sizes:
+            evs = [torch.from_numpy(blob_target(S, S, 910000 + i) if i % 2 == 0
+                                    else noise_target(S, S, 910000 + i)).to(dev) for i in range(4)]
+            extra[str(S)] = evaluate(net, evs)
     finally:
         holo.ws_net_destroy(net)
     log(f"targets {t1 - t0:.1f}s, GS labels {t2 - t1:.1f}s, training {t3 - t2:.1f}s")
-    return {"losses": losses, "eval": rows, "seconds": {"targets": t1 - t0, "labels": t2 - t1, "train": t3 - t2}}
+    return {"losses": losses, "eval": rows, "eval_other_sizes": extra,
+            "seconds": {"targets": t1 - t0, "labels": t2 - t1, "train": t3 - t2}}
