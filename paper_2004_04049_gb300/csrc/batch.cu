@@ -159,6 +159,7 @@ struct holo_graph {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int device;
+    int64_t kernels;   // kernels one launch replays (launch accounting)
 };
 
 extern "C" int ospr_batch_workspace_size(const holo_frame_desc* h_frames, int n_frames, int precision,
@@ -209,7 +210,11 @@ extern "C" int ospr_batch_graph_create(const holo_frame_desc* h_frames, int n_fr
         cudaStreamDestroy(cs);
         return cuda_status(e, "graph: begin capture");
     }
+    uint64_t before = 0, after = 0;
+    holo_launch_count(&before);
     rc = run_batch(h_frames, n_frames, precision, d_ws, ws_bytes, cs, pl);
+    holo_launch_count(&after);
+    add_launches(-int64_t(after - before));   // captured, not run
     e = cudaStreamEndCapture(cs, &graph);
     profiling_swap(prof);
     cudaStreamDestroy(cs);
@@ -223,7 +228,7 @@ extern "C" int ospr_batch_graph_create(const holo_frame_desc* h_frames, int n_fr
         cudaGraphDestroy(graph);
         return cuda_status(e, "graph: instantiate");
     }
-    holo_graph* g = new holo_graph{graph, exec, dev};
+    holo_graph* g = new holo_graph{graph, exec, dev, int64_t(after - before)};
     *out = g;
     return HOLO_OK;
 }
@@ -231,7 +236,9 @@ extern "C" int ospr_batch_graph_create(const holo_frame_desc* h_frames, int n_fr
 extern "C" int holo_graph_launch(holo_graph* g, holo_stream_t s) {
     clear_error();
     if (!g) return fail(HOLO_EINVAL, "holo_graph_launch: NULL graph");
-    return cuda_status(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(s)), "holo_graph_launch");
+    const int rc = cuda_status(cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(s)), "holo_graph_launch");
+    if (!rc) add_launches(g->kernels);
+    return rc;
 }
 
 extern "C" int holo_graph_destroy(holo_graph* g) {

@@ -104,6 +104,8 @@ int Launch::done(const char* what, cudaError_t launch) {
 
 int profiling_swap(int on) { return g_profiling.exchange(on ? 1 : 0); }
 
+void add_launches(int64_t n) { g_launches.fetch_add(uint64_t(n), std::memory_order_relaxed); }
+
 bool fault_injected(const char* kind) {
     const char* v = getenv("HOLO_FAULT_INJECT");
     if (!v || !*v) return false;

@@ -37,6 +37,8 @@ class Launch {
 
 // Sets event profiling on or off and returns the previous setting.
 int profiling_swap(int on);
+// Adjusts the launch count by n (kernels replayed by a graph, or captured and not run).
+void add_launches(int64_t n);
 
 // Host-side fault injection for tests: true when the environment variable
 // HOLO_FAULT_INJECT (a comma-separated list) names `kind` ("alloc": scratch allocations

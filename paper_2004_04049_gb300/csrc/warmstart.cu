@@ -66,6 +66,11 @@ struct ws_net {
     float* loss_scratch;
     float* loss_dev;
     int device;
+    // the batch-1 forward pass captured once as a CUDA graph (ws_infer): every buffer it
+    // touches belongs to the net, so later calls only replay it
+    cudaGraphExec_t infer_exec = nullptr;
+    cudaGraph_t infer_graph = nullptr;
+    int64_t infer_kernels = 0;   // kernels in the graph (launch accounting)
 };
 
 namespace {
@@ -322,6 +327,8 @@ extern "C" int ws_net_create(ws_net** out, uint64_t seed, int max_batch) {
 extern "C" int ws_net_destroy(ws_net* net) {
     clear_error();
     if (!net) return HOLO_OK;
+    if (net->infer_exec) cudaGraphExecDestroy(net->infer_exec);
+    if (net->infer_graph) cudaGraphDestroy(net->infer_graph);
     cudaFree(net->act_mem);
     cudaFree(net->param_mem);
     delete net;
@@ -385,7 +392,38 @@ extern "C" int ws_infer(ws_net* net, const float* d_target, int H, int W, float*
         return fail(HOLO_EINVAL, "ws_infer: target must be square, a multiple of %d (got %dx%d)", kRes, H, W);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
     if ((rc = prep_input(d_target, 1, H, W, kRes, kRes, net->x0, 8, st))) return rc;
-    if ((rc = forward(net, 1, st))) return rc;
+    if (!net->infer_exec) {
+        // one eager pass finishes every lazy set-up (shared-memory limits) outside the capture
+        if ((rc = forward(net, 1, st))) return rc;
+        if ((rc = cuda_status(cudaStreamSynchronize(st), "ws_infer: warm-up"))) return rc;
+        cudaStream_t cs = nullptr;
+        if ((rc = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "ws_infer: stream"))) return rc;
+        const int prof = profiling_swap(0);   // no event timing inside a capture
+        uint64_t before = 0, after = 0;
+        holo_launch_count(&before);
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = forward(net, 1, cs);
+            holo_launch_count(&after);
+            add_launches(-int64_t(after - before));   // captured, not run
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(cs, &g);
+            if (!rc && e == cudaSuccess) {
+                e = cudaGraphInstantiate(&net->infer_exec, g, 0);
+                if (e == cudaSuccess) net->infer_graph = g;
+                else cudaGraphDestroy(g);
+            } else if (g) {
+                cudaGraphDestroy(g);
+            }
+        }
+        profiling_swap(prof);
+        cudaStreamDestroy(cs);
+        if (rc) return rc;
+        if ((rc = cuda_status(e, "ws_infer: graph capture"))) return rc;
+        net->infer_kernels = int64_t(after - before);
+    }
+    if ((rc = cuda_status(cudaGraphLaunch(net->infer_exec, st), "ws_infer: graph launch"))) return rc;
+    add_launches(net->infer_kernels);
     return phase_out(net->out_f32, 8, kRes, kRes, H, W, d_phase_out, st);
 }
 
