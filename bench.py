@@ -221,6 +221,20 @@ def measured_traffic(family, kernel, grid_y):
         f"ncu capture of {kernel} grid {rec['grid']}: {rec['command']}"
 
 
+def measured_instructions(family, kernel, grid_y):
+    """Warp instructions of one launch from the ncu record (smsp__inst_executed.sum), or None."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)[family]
+    except (OSError, ValueError, KeyError):
+        return None
+    gy = rec.get("grid", "").strip("()").split(",")
+    if rec.get("sources") != sources_digest(family) or rec.get("kernel") != kernel or len(gy) < 2 \
+            or int(gy[1]) != grid_y:
+        return None
+    return rec.get("smsp__inst_executed.sum")
+
+
 def launch_signature(family, tuning, chunk, groups):
     """Template instance and grid.y of one float32 launch of an OSPR pass at H x W."""
     ci, cf, rv = tuning["col_ifft_variant"], tuning["col_fft_variant"], tuning["row_variant"]
@@ -361,6 +375,17 @@ def run_ours(args):
                                  for f in fams}}
     sf_bytes = np.mean([subframe_bytes(P, N_SF, L if L > 0 else N_SF * P) for L in L_SWEEP])
     path_gbs = value / world * sf_bytes / 1e9
+    # the same kernel against instruction issue: 4 warp instructions per SM per clock
+    insts = measured_instructions(dom, kname, grid_y) if kname else None
+    issue = None
+    if insts and n_dom:
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = 2070.0
+        peak_issue = sm_count * 4 * mhz * 1e6
+        got = insts / (ms_dom / n_dom / 1e3)
+        issue = {"bound": "issue", "achieved": got / 1e12, "peak": peak_issue / 1e12, "unit": "T warp-inst/s",
+                 "frac": got / peak_issue, "instructions_per_launch": insts,
+                 "peak_source": f"{sm_count} SMs x 4 schedulers x {mhz:.0f} MHz (maximum SM clock)"}
 
     # GS leg: 1024^2, 20 iterations, LUT-random start
     gcodes = torch.empty(GS_L, dtype=torch.uint8, device=dev)
@@ -443,6 +468,7 @@ def run_ours(args):
             "sequential": {"value": seq_value, "unit": "sub-frames/s", "ms_per_step": seq_total / args.steps,
                            "how": "the same step one frame at a time on one stream (per-frame API calls)"},
             "roofline": roofline,
+            "roofline_issue": issue,
             "path_bytes_model": {"bytes_per_subframe": sf_bytes, "achieved_GBps": path_gbs,
                                  "frac_of_hbm": path_gbs / peak_bw},
             "gs": {"metric": "GS 1024x1024 iterations/s (20 iterations, 256 levels, L=10007)",
