@@ -41,6 +41,8 @@ CASES = [
     (128, 128, 6, 0, "blob"),             # flat phase (L = 0)
     (128, 128, 4, holo.L_UNREPEATED, "blob"),
     (64, 64, 7, 1, "noise"),              # one entry: every pixel the same phase
+    (64, 4096, 3, 10007, "blob"),         # extreme aspect ratios: shortest columns, longest rows
+    (4096, 64, 2, 10007, "noise"),        # and the reverse
 ]
 
 
