@@ -465,6 +465,7 @@ def run_ours(args):
     batch = run_batch_leg(dev, stream) if not args.no_batch else None
     precision_leg = run_precision_leg(dev, stream) if not args.no_batch else None
     sources_leg = run_phase_source_leg(dev, stream) if not args.no_batch else None
+    fresnel_leg = run_fresnel_leg(dev, stream) if not args.no_batch else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -502,6 +503,7 @@ def run_ours(args):
             "batch": batch,
             "precision": precision_leg,
             "phase_sources": sources_leg,
+            "fresnel": fresnel_leg,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -649,6 +651,44 @@ def run_phase_source_leg(dev, stream, reps=10):
                      "table_build_us": build[1] / max(build[0], 1) * 1e3 if kind != "splitmix64" else 0.0,
                      "generation_pass_us": gen[1] / max(gen[0], 1) * 1e3}
     return out
+
+
+# ------------------------------------------------------------------ Fresnel leg ----
+def run_fresnel_leg(dev, stream, reps=10, kappa=2.4e-4):
+    """One 1024x1024 N=24 frame (L = 10007) with Fresnel propagation (kappa = pitch^2 /
+    (wavelength * z); 2.4e-4 is 8 um pixels, 532 nm light, z = 0.5 m) against the same frame
+    in the far field: the Fresnel field is not Hermitian, so every sub-frame takes its own
+    transforms."""
+    import torch
+
+    from paper_2004_04049_gb300 import holo, pipeline
+    from synthetic import blob_target
+
+    s = stream.cuda_stream
+    P = H * W
+    T = torch.from_numpy(blob_target(H, W, 1000)).to(dev)
+    lut = torch.empty(GS_L, dtype=torch.uint8, device=dev)
+    holo.lut_build(LUT_SEED, GS_L, 256, lut, None, stream=s)
+    ws = torch.empty(holo.ospr_fresnel_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
+    bits = torch.empty((N_SF, P // 32), dtype=torch.int32, device=dev)
+    I = torch.empty((H, W), dtype=torch.float32, device=dev)
+
+    def run():
+        holo.ospr_generate_fresnel(T, H, W, N_SF, lut, GS_L, 256, LUT_SEED, 0, 0, kappa, bits, I, ws,
+                                   stream=s)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        run()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": f"1024x1024, N={N_SF}, L={GS_L}, kappa={kappa}", "ms_per_frame": ms,
+            "subframes_per_s": N_SF / (ms / 1e3), "energy_per_pixel": float(I.sum().item()) / P}
 
 
 # --------------------------------------------------------- mixed precision leg ----

@@ -79,7 +79,7 @@ int holo_launch_count(uint64_t* out_count);
  * launch while enabled. holo_profile_read synchronises the recorded events and returns,
  * for the kernel family `name`, the number of launches and their summed duration in
  * milliseconds since the last holo_profile_reset. Families: "lut_build",
- * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "gs_prepare",
+ * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "fresnel_chirp", "gs_prepare",
  * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2", "lfsr_build",
  * "nn_conv_fwd", "nn_conv_dgrad", "nn_conv_wgrad", "nn_elementwise",
  * "nn_loss", "nn_adam". */
@@ -230,6 +230,38 @@ int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
                           const uint8_t* d_codes, int64_t L, int levels, uint64_t seed,
                           int64_t start_index, int64_t subframe_stride, int precision,
                           uint32_t* d_holo_bits, float* d_replay, holo_stream_t s);
+
+/* --------------------------------------------------- Fresnel propagation ---- */
+
+/*
+ * ospr_fresnel_workspace_size - bytes of device workspace ospr_generate_fresnel needs.
+ */
+int ospr_fresnel_workspace_size(int H, int W, int N, size_t* bytes);
+
+/*
+ * ospr_generate_fresnel - OSPR with Fresnel instead of far-field propagation (Section 2
+ * names both regimes; the paper's experiments use the far field). Model: the replay of a
+ * hologram h is |DFT(h * Q)|^2 with the separable quadratic phase
+ *     Q(y, x) = exp(i*pi*kappa*((x - W/2)^2 + (y - H/2)^2)),  kappa = pitch^2 / (wavelength * z),
+ * the replay plane's own quadratic phase being invisible to an intensity replay (the
+ * random target phase is drawn relative to it). Per sub-frame s:
+ *     E_s = T * exp(i*theta_s)  (the draw rule of ospr_generate),
+ *     H_s = conj(Q) * IDFT(E_s), h_s = +1 where Re H_s >= 0 else -1,
+ *     I   = (1/N) sum_s |DFT(h_s * Q)|^2  (unitary transforms).
+ * kappa = 0 is the far field of ospr_generate. The Fresnel field is not Hermitian, so
+ * every sub-frame takes its own transforms (twice the work of ospr_generate per
+ * sub-frame) and the replay has no twin symmetry.
+ *   d_target ... subframe_stride, d_holo_bits, d_replay, stream: as for ospr_generate.
+ *   kappa       finite, |kappa| <= 1e6 (pixel pitch^2 / (wavelength * distance)).
+ *   d_ws        device workspace of at least ospr_fresnel_workspace_size() bytes,
+ *               256-byte aligned; it also holds the H + W chirp factors of Q, made on the
+ *               device at the start of the call (float64 sincospi rounded to float32).
+ * Float32 only (tile variants, pairs in flight and accumulators follow the shape's OSPR
+ * tuning). Returns HOLO_EINVAL / HOLO_EUNSUPPORTED / HOLO_EWORKSPACE on bad arguments.
+ */
+int ospr_generate_fresnel(const float* d_target, int H, int W, int N, const uint8_t* d_codes, int64_t L,
+                          int levels, uint64_t seed, int64_t start_index, int64_t subframe_stride, double kappa,
+                          uint32_t* d_holo_bits, float* d_replay, void* d_ws, size_t ws_bytes, holo_stream_t s);
 
 /* ------------------------------------------------------- batched frames ---- */
 

@@ -52,6 +52,31 @@ __global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, 
     I[pm] = s;
 }
 
+// Fresnel replay: no twin symmetry, I(k) = scale * sum_g S_g(k)
+__global__ void k_ospr_finalize_fresnel(const float* __restrict__ S, int groups, size_t P, float scale,
+                                        float* __restrict__ I) {
+    pdl_wait();
+    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float s = 0.f;
+    for (int g = 0; g < groups; ++g) s += S[size_t(g) * P + p];
+    I[p] = s * scale;
+}
+
+// The separable quadratic phase of Fresnel propagation, chirp[i] = exp(i*pi*kappa*(i - n/2)^2)
+// for the H rows and then the W columns, evaluated in float64 (sincospi reduces the
+// argument exactly) and rounded to float32.
+__global__ void k_fresnel_chirp(int H, int W, double kappa, float2* __restrict__ chirp) {
+    pdl_wait();   // a previous kernel may still read the table
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= H + W) return;
+    const int n = i < H ? H : W;
+    const double d = double(i < H ? i : i - H) - 0.5 * double(n);
+    double sn, cs;
+    sincospi(kappa * d * d, &sn, &cs);
+    chirp[i] = make_float2(float(cs), float(sn));
+}
+
 // ------------------------------------------------------------------- host ----
 // Per-shape tuning: tile variants of the three passes (column IDFT, row, column DFT;
 // the two column passes share only the field layout, so their tiles are independent),
@@ -207,6 +232,16 @@ static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_repla
             if (replay && (rc = ospr_run_col_fft_tc(a, pl.prec, st))) return rc;
         }
     }
+    if (replay && a.fresnel) {
+        const size_t P = size_t(a.H) * a.W;
+        const float scale = float(1.0 / (double(a.N) * double(P)));
+        const int threads = 256;
+        Launch ln("ospr_finalize", st);
+        const cudaError_t le = launch_pdl(k_ospr_finalize_fresnel, dim3(unsigned((P + threads - 1) / threads)),
+                                          dim3(threads), 0, st, static_cast<const float*>(a.sacc), pl.groups, P,
+                                          scale, d_replay);
+        return ln.done("ospr_finalize launch", le);
+    }
     if (replay) {
         const size_t P = size_t(a.H) * a.W;
         const float scale = float(1.0 / (2.0 * double(a.N) * double(P)));
@@ -278,6 +313,8 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.cs256 = tab.cs256;
     a.tc = tab.tc[precision];
     a.tc05b = tab.tc05b[precision];
+    a.fresnel = 0;
+    a.chirp_y = a.chirp_x = nullptr;
     if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
     // Section 8 design rules: warnings only
     if (L > 0) {
@@ -286,6 +323,81 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
         if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
     }
     return HOLO_OK;
+}
+
+// Fresnel propagation: one sub-frame per field slot, so the plan of 2N sub-frames gives N
+// slots; the chirp tables (H + W complex64) follow the plan's buffers.
+static OsprPlan fresnel_plan(int H, int W, int N, size_t* chirp_off) {
+    OsprPlan pl = ospr_plan(H, W, 2 * N, HOLO_FP32);
+    *chirp_off = pl.total;
+    pl.total += align_up(size_t(H + W) * sizeof(float2), 256);
+    return pl;
+}
+
+extern "C" int ospr_fresnel_workspace_size(int H, int W, int N, size_t* bytes) {
+    clear_error();
+    if (!bytes) return fail(HOLO_EINVAL, "ospr_fresnel_workspace_size: NULL output");
+    int rc = check_shape("ospr_fresnel_workspace_size", H, W);
+    if (rc) return rc;
+    if (N < 1 || N > 4096) return fail(HOLO_EINVAL, "ospr_fresnel_workspace_size: N=%d out of [1, 4096]", N);
+    size_t off = 0;
+    *bytes = fresnel_plan(H, W, N, &off).total;
+    return HOLO_OK;
+}
+
+extern "C" int ospr_generate_fresnel(const float* d_target, int H, int W, int N, const uint8_t* d_codes, int64_t L,
+                                     int levels, uint64_t seed, int64_t start_index, int64_t subframe_stride,
+                                     double kappa, uint32_t* d_holo_bits, float* d_replay, void* d_ws,
+                                     size_t ws_bytes, holo_stream_t s) {
+    clear_error();
+    const char* who = "ospr_generate_fresnel";
+    int rc = check_shape(who, H, W);
+    if (rc) return rc;
+    if (N < 1 || N > 4096) return fail(HOLO_EINVAL, "%s: N=%d out of [1, 4096]", who, N);
+    if (!std::isfinite(kappa) || std::fabs(kappa) > 1e6) return fail(HOLO_EINVAL, "%s: kappa %g", who, kappa);
+    if (!d_target) return fail(HOLO_EINVAL, "%s: d_target is NULL", who);
+    if (!d_holo_bits && !d_replay) return fail(HOLO_EINVAL, "%s: both outputs are NULL", who);
+    const int64_t P = int64_t(H) * W;
+    const int64_t stride = subframe_stride == 0 ? P : subframe_stride;
+    if (stride > (INT64_C(1) << 40) || start_index > (INT64_C(1) << 61))
+        return fail(HOLO_EINVAL, "%s: start or stride too large", who);
+    PhaseSource ps;
+    rc = make_phase_source(who, d_codes, L, levels, seed, start_index, stride, &ps);
+    if (rc) return rc;
+    size_t chirp_off = 0;
+    const OsprPlan pl = fresnel_plan(H, W, N, &chirp_off);
+    if (!d_ws || ws_bytes < pl.total)
+        return fail(HOLO_EWORKSPACE, "%s: workspace %zu bytes, need %zu", who, ws_bytes, pl.total);
+    if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0)
+        return fail(HOLO_EWORKSPACE, "%s: workspace is not 256-byte aligned", who);
+    Tables tab;
+    if ((rc = device_tables(&tab))) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    float2* chirp = reinterpret_cast<float2*>(static_cast<char*>(d_ws) + chirp_off);
+    {
+        Launch ln("fresnel_chirp", st);
+        const cudaError_t le = launch_pdl(k_fresnel_chirp, dim3(unsigned((H + W + 255) / 256)), dim3(256), 0, st, H,
+                                          W, kappa, chirp);
+        if ((rc = ln.done("fresnel_chirp launch", le))) return rc;
+    }
+    OsprArgs a;
+    a.target = d_target;
+    a.H = H;
+    a.W = W;
+    a.N = N;
+    a.ps = ps;
+    a.zbuf = static_cast<float2*>(d_ws);
+    a.sacc = reinterpret_cast<float*>(static_cast<char*>(d_ws) + pl.z_bytes);
+    a.groups = pl.groups;
+    a.bits = d_holo_bits;
+    a.tw = tab.twiddles;
+    a.cs256 = tab.cs256;
+    a.tc = nullptr;
+    a.tc05b = nullptr;
+    a.fresnel = 1;
+    a.chirp_y = chirp;
+    a.chirp_x = chirp + H;
+    return ospr_run(a, pl, d_replay != nullptr, d_replay, st);
 }
 
 extern "C" int ospr_tuning_get(int H, int W, int* col_ifft_variant, int* col_fft_variant, int* row_variant,
@@ -512,6 +624,8 @@ extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
     a.bits = d_holo_bits;
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
+    a.fresnel = 0;
+    a.chirp_y = a.chirp_x = nullptr;
     // every scratch byte a kernel reads was written earlier in this call (the first chunk
     // overwrites the accumulator), so nothing needs clearing between calls
     return ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s));

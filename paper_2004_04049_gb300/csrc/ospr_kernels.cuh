@@ -82,7 +82,19 @@ struct OsprArgs {
     const float2* cs256;
     const TcFrags* tc;    // DFT-32 A fragments of the tensor-core precision in use
     const uint8_t* tc05b; // tcgen05 DFT-32 matrices of that precision ([direction][hi, lo])
+    // Fresnel propagation: one sub-frame per field slot (no two-for-one packing) and the
+    // quadratic phase Q(y, x) = chirp_y[y] * chirp_x[x]; 0 / null for the far field
+    int fresnel;
+    const float2* chirp_y;   // [H] exp(i*pi*kappa*(y - H/2)^2)
+    const float2* chirp_x;   // [W] exp(i*pi*kappa*(x - W/2)^2)
 };
+
+// first sub-frame of field slot `slot` and whether the slot holds one sub-frame only
+__device__ __forceinline__ int slot_subframe(const OsprArgs& a, int slot, bool& single) {
+    const int s0 = (a.fresnel ? 1 : 2) * (a.first_pair + slot);
+    single = a.fresnel || s0 + 1 >= a.N;
+    return s0;
+}
 
 template <int NC, int V>
 constexpr int col_stride() { return col_line_stride(NC, ColCfg<NC, V>::R, ColCfg<NC, V>::LPC); }
@@ -298,8 +310,8 @@ k_ospr_col_ifft(OsprArgs a) {
     const int W = a.W;
     int c, pl;
     mirror_column<LPC>(blockIdx.x, lc, W, c, pl);
-    const int s0 = 2 * (a.first_pair + int(blockIdx.y));
-    const bool single = s0 + 1 >= a.N;   // uniform over the CTA
+    bool single;   // uniform over the CTA
+    const int s0 = slot_subframe(a, int(blockIdx.y), single);
     float2* xline = lines + pl * S;
     float2 v[R];
     if (a.ps.mode == kPhaseTable) {
@@ -327,7 +339,9 @@ k_ospr_col_ifft(OsprArgs a) {
 }
 
 // ------------------------------------------------------------------ pass 2 ----
-template <int NR, int V, bool REPLAY, int PREC>
+// FRESNEL: the row holds one sub-frame's IDFT(E); the hologram field is conj(Q) * IDFT(E),
+// binarised on its real part, and the replay transform takes h * Q.
+template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL = false>
 __global__ void __launch_bounds__((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR)
 k_ospr_row(OsprArgs a) {
     constexpr int R = RowCfg<NR, V>::R, T = NR / R;
@@ -336,8 +350,8 @@ k_ospr_row(OsprArgs a) {
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * RowCfg<NR, V>::LPR + line;
-    const int s0 = 2 * (a.first_pair + int(blockIdx.y));
-    const bool single = s0 + 1 >= a.N;
+    bool single;
+    const int s0 = slot_subframe(a, int(blockIdx.y), single);
     const size_t P = size_t(a.H) * NR;
     float2* z = a.zbuf + size_t(blockIdx.y) * P + size_t(r) * NR;
     pdl_wait();
@@ -346,9 +360,16 @@ k_ospr_row(OsprArgs a) {
     for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
     row_line_fft<NR, V, +1, PREC>(v, sm, line, t, a);
 
+    float2 qy = make_float2(1.f, 0.f);
+    if constexpr (FRESNEL) qy = __ldg(a.chirp_y + r);
     const size_t words = P / 32;
 #pragma unroll
     for (int e = 0; e < R; ++e) {
+        float2 q = make_float2(1.f, 0.f);
+        if constexpr (FRESNEL) {
+            q = cmul(qy, __ldg(a.chirp_x + t + T * e));
+            v[e].x = fmaf(v[e].x, q.x, v[e].y * q.y);   // Re(IDFT(E) * conj(Q))
+        }
         const bool n0 = v[e].x < 0.f;
         const bool n1 = v[e].y < 0.f;
         if (a.bits) {
@@ -360,7 +381,8 @@ k_ospr_row(OsprArgs a) {
                 if (!single) a.bits[size_t(s0 + 1) * words + w] = b1;
             }
         }
-        v[e] = make_float2(n0 ? -1.f : 1.f, single ? 0.f : (n1 ? -1.f : 1.f));
+        if constexpr (FRESNEL) v[e] = n0 ? make_float2(-q.x, -q.y) : q;   // h * Q
+        else v[e] = make_float2(n0 ? -1.f : 1.f, single ? 0.f : (n1 ? -1.f : 1.f));
     }
     if constexpr (REPLAY) {
         row_line_fft<NR, V, -1, PREC>(v, sm, line, t, a);

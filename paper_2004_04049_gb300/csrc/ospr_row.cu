@@ -4,21 +4,23 @@
 
 namespace holo {
 
-template <int NR, int V, bool REPLAY>
+template <int NR, int V, bool REPLAY, bool FRESNEL>
 static int launch_row(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
     constexpr size_t smem = row_smem_bytes<NR, V>();
-    int rc = ensure_smem((const void*)k_ospr_row<NR, V, REPLAY, 0>, smem, &mask);
+    int rc = ensure_smem((const void*)k_ospr_row<NR, V, REPLAY, 0, FRESNEL>, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.H / RowCfg<NR, V>::LPR, a.pairs);
     Launch ln("ospr_row", st);
-    const cudaError_t le = launch_pdl(k_ospr_row<NR, V, REPLAY, 0>, grid, dim3((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR), smem, st, a);
+    const cudaError_t le = launch_pdl(k_ospr_row<NR, V, REPLAY, 0, FRESNEL>, grid,
+                                      dim3((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR), smem, st, a);
     return ln.done("ospr_row launch", le);
 }
 
 template <int NR, int V>
 static int launch_row_any(const OsprArgs& a, bool replay, cudaStream_t st) {
-    return replay ? launch_row<NR, V, true>(a, st) : launch_row<NR, V, false>(a, st);
+    if (a.fresnel) return replay ? launch_row<NR, V, true, true>(a, st) : launch_row<NR, V, false, true>(a, st);
+    return replay ? launch_row<NR, V, true, false>(a, st) : launch_row<NR, V, false, false>(a, st);
 }
 
 int ospr_run_row(const OsprArgs& a, int v, bool replay, cudaStream_t st) {

@@ -73,6 +73,11 @@ _SIGS = {
                                  _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
                                  _c.c_int64, _c.c_int64, _c.c_int,
                                  _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "ospr_fresnel_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "ospr_generate_fresnel": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int,
+                                         _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
+                                         _c.c_int64, _c.c_int64, _c.c_double,
+                                         _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
     "ospr_generate_noalloc": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int,
                                          _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64,
                                          _c.c_int64, _c.c_int64, _c.c_int,
@@ -231,6 +236,21 @@ def ospr_generate(d_target, H, W, N, d_codes, L, levels, seed, start_index, subf
         ws_bytes = d_ws.numel() * d_ws.element_size()
     return _call("ospr_generate", _ptr(d_target), H, W, N, _ptr(d_codes), L, levels, seed,
                  start_index, subframe_stride, precision, _ptr(d_holo_bits), _ptr(d_replay),
+                 _ptr(d_ws), ws_bytes, _stream(stream, d_target))
+
+
+def ospr_fresnel_workspace_size(H, W, N):
+    b = ctypes.c_size_t(0)
+    _call("ospr_fresnel_workspace_size", H, W, N, ctypes.byref(b))
+    return b.value
+
+
+def ospr_generate_fresnel(d_target, H, W, N, d_codes, L, levels, seed, start_index, subframe_stride,
+                          kappa, d_holo_bits, d_replay, d_ws, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("ospr_generate_fresnel", _ptr(d_target), H, W, N, _ptr(d_codes), L, levels, seed,
+                 start_index, subframe_stride, float(kappa), _ptr(d_holo_bits), _ptr(d_replay),
                  _ptr(d_ws), ws_bytes, _stream(stream, d_target))
 
 

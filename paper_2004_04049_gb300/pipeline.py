@@ -36,6 +36,21 @@ def ospr(target, N, codes=None, L=0, levels=256, seed=0, start=0, stride=0, bits
     return b, r
 
 
+def ospr_fresnel(target, N, kappa, codes=None, L=0, levels=256, seed=0, start=0, stride=0, bits=True,
+                 replay=True, ws=None, stream=None):
+    """OSPR with Fresnel propagation; returns (bits int32 [N, H*W/32] or None, replay or None)."""
+    H, W = target.shape
+    dev = target.device
+    need = holo.ospr_fresnel_workspace_size(H, W, N)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, dev)
+    b = torch.empty((N, H * W // 32), dtype=torch.int32, device=dev) if bits else None
+    r = torch.empty((H, W), dtype=torch.float32, device=dev) if replay else None
+    holo.ospr_generate_fresnel(target, H, W, N, codes, L, levels, seed, start, stride, kappa, b, r, ws,
+                               ws.numel(), stream=stream)
+    return b, r
+
+
 def gs(target, iters, levels=256, codes=None, L=0, lut_levels=256, seed=0, start=0,
        init_phase=None, state_in=None, want_state=False, want_codes=True, want_replay=True,
        ws=None, precision=holo.HOLO_FP32, stream=None):
