@@ -21,12 +21,17 @@ Iteration k = 1..K:
     H = IDFT(E);  q = quantise(arg H);  h = exp(i*2*pi*q/levels);  R = DFT(h);
     eps_k = sum (|R| - T_s)^2;  E = T_s * exp(i*arg R)
 Returns the codes q and intensity |R|^2 of the last iteration and all eps_k.
+
+Fresnel propagation (``gs_fresnel``): the same iteration with the propagation pair of
+the Fresnel model in ospr.py, H = conj(Q) * IDFT(E) and R = DFT(h * Q); both are unitary,
+so the projection argument behind the non-increasing error carries over.
 """
 
 import numpy as np
 
 from . import fft as _fft
 from . import lut as _lut
+from .ospr import fresnel_chirp
 
 
 def energy_scaled_target(target):
@@ -93,5 +98,28 @@ def gs(target, iters, table, L, seed, start=0, levels=256, init_phase=None, init
     q = R = None
     for _ in range(iters):
         q, R, eps, E = gs_step(E, Ts, levels)
+        errs.append(eps)
+    return q, np.abs(R) ** 2, np.array(errs), E
+
+
+def gs_step_fresnel(E, Ts, kappa, levels=256):
+    """One GS iteration under Fresnel propagation. Returns (q, R, eps, E_next)."""
+    H, W = np.asarray(E).shape
+    Q = fresnel_chirp(H, W, kappa)
+    Hf = np.conj(Q) * _fft.ifft2(E)
+    q = quantise_phase(Hf, levels)
+    R = _fft.fft2(hologram_of_codes(q, levels) * Q)
+    eps = float(np.sum((np.abs(R) - Ts) ** 2))
+    return q, R, eps, amplitude_constraint(R, Ts)
+
+
+def gs_fresnel(target, iters, table, L, seed, kappa, start=0, levels=256, init_phase=None, lut_levels=256):
+    """K iterations under Fresnel propagation; returns as ``gs``."""
+    Ts = energy_scaled_target(target)
+    E = initial_field(target, table, L, seed, start, lut_levels, init_phase)
+    errs = []
+    q = R = None
+    for _ in range(iters):
+        q, R, eps, E = gs_step_fresnel(E, Ts, kappa, levels)
         errs.append(eps)
     return q, np.abs(R) ** 2, np.array(errs), E

@@ -12,12 +12,14 @@ What would catch a dropped chirp, a chirp of the wrong sign or a transposed rast
   * unitarity: every sub-frame's replay energy equals P;
   * a real hologram's Fourier replay is centrosymmetric (twin image); its Fresnel replay
     is not, so a chirp missing from the replay breaks this pin.
+GS under Fresnel propagation: kappa = 0 is the far-field GS oracle; one iteration equals
+the explicit sums (inverse and forward, term by term); the error never increases.
 """
 
 import numpy as np
 import pytest
 
-from oracle import lut, ospr
+from oracle import gs, lut, ospr
 from synthetic import blob_target
 
 
@@ -90,3 +92,54 @@ def test_bits_follow_the_binarised_field():
     for s in range(2):
         assert np.array_equal(ospr.unpack_bits(bits[s], 256), np.where(extra["re_h"][s].reshape(-1) >= 0, 1.0, -1.0))
     np.testing.assert_allclose(ospr.replay_from_bits_fresnel(bits, 16, 16, 0.02), I, rtol=1e-12)
+
+
+def _inverse_fresnel_by_sum(E, kappa):
+    """conj(Q(y,x)) * P^-1/2 sum_{u,v} E(u,v) exp(+2*pi*i*(u*y/H + v*x/W)), term by term."""
+    H, W = E.shape
+    out = np.zeros((H, W), dtype=complex)
+    for y in range(H):
+        for x in range(W):
+            acc = 0.0 + 0.0j
+            for u in range(H):
+                for v in range(W):
+                    ang = 2.0 * np.pi * (u * y / H + v * x / W)
+                    acc += E[u, v] * complex(np.cos(ang), np.sin(ang))
+            q = np.pi * kappa * ((x - W / 2) ** 2 + (y - H / 2) ** 2)
+            out[y, x] = acc * complex(np.cos(q), -np.sin(q)) / np.sqrt(H * W)
+    return out
+
+
+def test_gs_kappa_zero_is_the_far_field_oracle():
+    T = blob_target(32, 32, 1000)
+    table = lut.lut_codes(7, 1031)
+    q0, I0, e0, _ = gs.gs(T, 4, table, 1031, 7)
+    q1, I1, e1, _ = gs.gs_fresnel(T, 4, table, 1031, 7, 0.0)
+    assert np.array_equal(q0, q1)
+    np.testing.assert_allclose(e1, e0, rtol=1e-12)
+    np.testing.assert_allclose(I1, I0, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("levels", [256, 2])
+def test_gs_step_equals_explicit_sums(levels):
+    H, W, kappa = 4, 8, 0.093
+    rng = np.random.default_rng(5)
+    T = rng.random((H, W)) + 0.1
+    Ts = gs.energy_scaled_target(T)
+    E = Ts * np.exp(1j * 2 * np.pi * rng.random((H, W)))
+    q, R, eps, En = gs.gs_step_fresnel(E, Ts, kappa, levels)
+    Hf = _inverse_fresnel_by_sum(E, kappa)
+    q_ref = gs.quantise_phase(Hf, levels)
+    assert np.array_equal(q, q_ref)
+    h = gs.hologram_of_codes(q_ref, levels)
+    I_ref = _fresnel_replay_by_sum(h, kappa)
+    np.testing.assert_allclose(np.abs(R) ** 2, I_ref, rtol=1e-10, atol=1e-10)
+    assert eps == pytest.approx(float(np.sum((np.sqrt(I_ref) - Ts) ** 2)), rel=1e-10)
+
+
+@pytest.mark.parametrize("levels", [256, 2])
+def test_gs_fresnel_error_never_increases(levels):
+    T = blob_target(32, 64, 1003)
+    table = lut.lut_codes(5, 4099)
+    _, _, eps, _ = gs.gs_fresnel(T, 12, table, 4099, 5, 0.004, levels=levels)
+    assert np.all(np.diff(eps) <= 1e-9 * eps[0]), eps
