@@ -687,8 +687,29 @@ def run_fresnel_leg(dev, stream, reps=10, kappa=2.4e-4):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    return {"workload": f"1024x1024, N={N_SF}, L={GS_L}, kappa={kappa}", "ms_per_frame": ms,
-            "subframes_per_s": N_SF / (ms / 1e3), "energy_per_pixel": float(I.sum().item()) / P}
+    out = {"workload": f"1024x1024, N={N_SF}, L={GS_L}, kappa={kappa}", "ms_per_frame": ms,
+           "subframes_per_s": N_SF / (ms / 1e3), "energy_per_pixel": float(I.sum().item()) / P}
+    # GS under Fresnel propagation: 20 iterations from the LUT start, as the far-field GS leg
+    gws = torch.empty(holo.gs_workspace_size(H, W, GS_ITERS), dtype=torch.uint8, device=dev)
+    q = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    err = torch.empty(GS_ITERS, dtype=torch.float64, device=dev)
+
+    def run_gs():
+        holo.gs_iterate_fresnel(T, H, W, GS_ITERS, 256, None, lut, GS_L, 256, LUT_SEED, 0, kappa, q, I, err, None,
+                                None, gws, stream=s)
+
+    for _ in range(3):
+        run_gs()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        run_gs()
+    e1.record(stream)
+    e1.synchronize()
+    gms = e0.elapsed_time(e1) / reps
+    out["gs"] = {"iters": GS_ITERS, "ms_per_run": gms, "iter_per_s": GS_ITERS / (gms / 1e3),
+                 "eps_per_pixel_after_iters": float(err[-1].item()) / P}
+    return out
 
 
 # --------------------------------------------------------- mixed precision leg ----

@@ -326,7 +326,8 @@ int holo_graph_destroy(holo_graph* g);
 /* --------------------------------------------------------------------- GS ---- */
 
 /*
- * gs_workspace_size - bytes of device workspace gs_iterate needs.
+ * gs_workspace_size - bytes of device workspace gs_iterate and gs_iterate_fresnel need
+ * (the complex field, scalars, error partials and the H + W Fresnel chirp factors).
  */
 int gs_workspace_size(int H, int W, int iters, int precision, size_t* bytes);
 
@@ -360,6 +361,20 @@ int gs_iterate(const float* d_target, int H, int W, int iters, int levels,
                uint8_t* d_phase_codes, float* d_replay, double* d_err,
                const float* d_state_in, float* d_state_out,
                void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/*
+ * gs_iterate_fresnel - gs_iterate under Fresnel propagation (Section 2 names both regimes;
+ * the quadratic-phase model and kappa are those of ospr_generate_fresnel): per iteration
+ *   H = conj(Q) * IDFT(E); q and h as gs_iterate; R = DFT(h * Q); eps_k and E as gs_iterate,
+ * Q(y, x) = exp(i*pi*kappa*((x - W/2)^2 + (y - H/2)^2)). kappa = 0 gives the results of
+ * gs_iterate. Float32; every other argument as gs_iterate; HOLO_EINVAL for a kappa that is
+ * not finite or above 1e6 in magnitude.
+ */
+int gs_iterate_fresnel(const float* d_target, int H, int W, int iters, int levels,
+                       const float* d_init_phase, const uint8_t* d_codes, int64_t L, int lut_levels,
+                       uint64_t seed, int64_t start_index, double kappa, uint8_t* d_phase_codes,
+                       float* d_replay, double* d_err, const float* d_state_in, float* d_state_out,
+                       void* d_ws, size_t ws_bytes, holo_stream_t s);
 
 /*
  * GS tile variants per shape (an engineering choice, not part of the method): the column

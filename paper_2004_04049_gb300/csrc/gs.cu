@@ -84,6 +84,9 @@ struct GsArgs {
     const float2* tw;
     const float2* cs256;
     float inv_sqrt_p;
+    // Fresnel propagation: Q(y, x) = chirp_y[y] * chirp_x[x] (null for the far field)
+    const float2* chirp_y;
+    const float2* chirp_x;
 };
 
 template <int NC, int V>
@@ -164,7 +167,8 @@ k_gs_col_init(GsArgs a) {
 }
 
 // -------------------------------------------------------------------- row ----
-template <int NR, int V>
+// FRESNEL: the hologram field is conj(Q) * IDFT(E) and the replay transform takes h * Q.
+template <int NR, int V, bool FRESNEL = false>
 __global__ void __launch_bounds__((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR)
 k_gs_row(GsArgs a) {
     constexpr int R = GsRowCfg<NR, V>::R, T = NR / R;
@@ -186,12 +190,20 @@ k_gs_row(GsArgs a) {
     const int levels = 1 << a.levels_bits;
     const float k_code = float(levels) * 0.15915494309189533577f;   // levels / (2 pi)
     const int shift = 8 - a.levels_bits;
+    float2 qy = make_float2(1.f, 0.f);
+    if constexpr (FRESNEL) qy = __ldg(a.chirp_y + r);
 #pragma unroll
     for (int e = 0; e < R; ++e) {
+        float2 qc = make_float2(1.f, 0.f);
+        if constexpr (FRESNEL) {
+            qc = cmul(qy, __ldg(a.chirp_x + t + T * e));
+            v[e] = make_float2(fmaf(v[e].x, qc.x, v[e].y * qc.y), fmaf(v[e].y, qc.x, -v[e].x * qc.y));
+        }
         const float ang = atan2f(v[e].y, v[e].x);
         const int q = int(floorf(fmaf(ang, k_code, 0.5f))) & (levels - 1);
         if (a.codes_out) a.codes_out[size_t(r) * NR + t + T * e] = uint8_t(q);
         v[e] = cs_lookup(cs, uint32_t(q) << shift);
+        if constexpr (FRESNEL) v[e] = cmul(v[e], qc);
     }
     line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
     pdl_trigger();
@@ -299,16 +311,20 @@ static int launch_col_init(const GsArgs& a, cudaStream_t st) {
                smem, st, a);
     return ln.done("gs_col_init launch", le);
 }
-template <int NR, int V>
-static int launch_row(const GsArgs& a, cudaStream_t st) {
+template <int NR, int V, bool FRESNEL>
+static int launch_row_kind(const GsArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
     constexpr size_t smem = gs_row_smem<NR, V>();
-    int rc = ensure_smem((const void*)k_gs_row<NR, V>, smem, &mask);
+    int rc = ensure_smem((const void*)k_gs_row<NR, V, FRESNEL>, smem, &mask);
     if (rc) return rc;
     Launch ln("gs_row", st);
-    const cudaError_t le = launch_pdl(k_gs_row<NR, V>, dim3(a.H / GsRowCfg<NR, V>::LPR), dim3((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR),
-               smem, st, a);
+    const cudaError_t le = launch_pdl(k_gs_row<NR, V, FRESNEL>, dim3(a.H / GsRowCfg<NR, V>::LPR),
+                                      dim3((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR), smem, st, a);
     return ln.done("gs_row launch", le);
+}
+template <int NR, int V>
+static int launch_row(const GsArgs& a, cudaStream_t st) {
+    return a.chirp_y ? launch_row_kind<NR, V, true>(a, st) : launch_row_kind<NR, V, false>(a, st);
 }
 template <int NC, int V>
 static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
@@ -359,7 +375,7 @@ static int col_blocks(int H, int W, int cv) {
 }
 
 struct GsLayout {
-    size_t y_off, sc_off, prep_off, err_off, total;
+    size_t y_off, sc_off, prep_off, err_off, chirp_off, total;
 };
 static GsLayout gs_layout(int H, int W, int iters) {
     GsLayout l;
@@ -369,7 +385,9 @@ static GsLayout gs_layout(int H, int W, int iters) {
     l.prep_off = l.sc_off + align_up(sizeof(GsScalars), 256);
     l.err_off = l.prep_off + align_up(sizeof(ff) * kGsPrepBlocks, 256);
     // error partials for the column tiles with the fewest lines (any variant fits)
-    l.total = l.err_off + align_up(sizeof(ff) * size_t(iters) * size_t(W / kGsMinLpc), 256);
+    l.chirp_off = l.err_off + align_up(sizeof(ff) * size_t(iters) * size_t(W / kGsMinLpc), 256);
+    // the chirp factors of Fresnel propagation (gs_iterate_fresnel)
+    l.total = l.chirp_off + align_up(sizeof(float2) * size_t(H + W), 256);
     return l;
 }
 
@@ -395,15 +413,15 @@ extern "C" int gs_workspace_size(int H, int W, int iters, int precision, size_t*
     return HOLO_OK;
 }
 
-extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int levels,
-                          const float* d_init_phase,
-                          const uint8_t* d_codes, int64_t L, int lut_levels, uint64_t seed,
-                          int64_t start_index, int precision,
-                          uint8_t* d_phase_codes, float* d_replay, double* d_err,
-                          const float* d_state_in, float* d_state_out,
-                          void* d_ws, size_t ws_bytes, holo_stream_t s) {
+namespace holo {
+
+// gs_iterate and gs_iterate_fresnel; `fresnel` selects the propagation pair
+static int gs_iterate_impl(const char* who, const float* d_target, int H, int W, int iters, int levels,
+                           const float* d_init_phase, const uint8_t* d_codes, int64_t L, int lut_levels,
+                           uint64_t seed, int64_t start_index, int precision, bool fresnel, double kappa,
+                           uint8_t* d_phase_codes, float* d_replay, double* d_err, const float* d_state_in,
+                           float* d_state_out, void* d_ws, size_t ws_bytes, holo_stream_t s) {
     clear_error();
-    const char* who = "gs_iterate";
     int rc = gs_check_shape(who, H, W);
     if (rc) return rc;
     if (iters < 1 || iters > 100000) return fail(HOLO_EINVAL, "%s: iters=%d out of [1, 100000]", who, iters);
@@ -443,7 +461,15 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
     a.inv_sqrt_p = float(1.0 / std::sqrt(double(H) * double(W)));
+    a.chirp_y = a.chirp_x = nullptr;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    if (fresnel) {
+        if (!std::isfinite(kappa) || std::fabs(kappa) > 1e6) return fail(HOLO_EINVAL, "%s: kappa %g", who, kappa);
+        float2* chirp = reinterpret_cast<float2*>(ws + lay.chirp_off);
+        if ((rc = fresnel_chirp_build(H, W, kappa, chirp, st))) return rc;
+        a.chirp_y = chirp;
+        a.chirp_x = chirp + H;
+    }
 
     a.prep_part = reinterpret_cast<const ff*>(ws + lay.prep_off);
     {
@@ -475,6 +501,30 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
         if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
     }
     return HOLO_OK;
+}
+
+}  // namespace holo
+
+extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int levels,
+                          const float* d_init_phase,
+                          const uint8_t* d_codes, int64_t L, int lut_levels, uint64_t seed,
+                          int64_t start_index, int precision,
+                          uint8_t* d_phase_codes, float* d_replay, double* d_err,
+                          const float* d_state_in, float* d_state_out,
+                          void* d_ws, size_t ws_bytes, holo_stream_t s) {
+    return gs_iterate_impl("gs_iterate", d_target, H, W, iters, levels, d_init_phase, d_codes, L, lut_levels, seed,
+                           start_index, precision, false, 0.0, d_phase_codes, d_replay, d_err, d_state_in,
+                           d_state_out, d_ws, ws_bytes, s);
+}
+
+extern "C" int gs_iterate_fresnel(const float* d_target, int H, int W, int iters, int levels,
+                                  const float* d_init_phase, const uint8_t* d_codes, int64_t L, int lut_levels,
+                                  uint64_t seed, int64_t start_index, double kappa, uint8_t* d_phase_codes,
+                                  float* d_replay, double* d_err, const float* d_state_in, float* d_state_out,
+                                  void* d_ws, size_t ws_bytes, holo_stream_t s) {
+    return gs_iterate_impl("gs_iterate_fresnel", d_target, H, W, iters, levels, d_init_phase, d_codes, L,
+                           lut_levels, seed, start_index, HOLO_FP32, true, kappa, d_phase_codes, d_replay, d_err,
+                           d_state_in, d_state_out, d_ws, ws_bytes, s);
 }
 
 extern "C" int gs_tuning_set(int H, int W, int col_variant, int row_variant) {

@@ -77,6 +77,13 @@ __global__ void k_fresnel_chirp(int H, int W, double kappa, float2* __restrict__
     chirp[i] = make_float2(float(cs), float(sn));
 }
 
+int fresnel_chirp_build(int H, int W, double kappa, float2* d_chirp, cudaStream_t st) {
+    Launch ln("fresnel_chirp", st);
+    const cudaError_t le = launch_pdl(k_fresnel_chirp, dim3(unsigned((H + W + 255) / 256)), dim3(256), 0, st, H, W,
+                                      kappa, d_chirp);
+    return ln.done("fresnel_chirp launch", le);
+}
+
 // ------------------------------------------------------------------- host ----
 // Per-shape tuning: tile variants of the three passes (column IDFT, row, column DFT;
 // the two column passes share only the field layout, so their tiles are independent),
@@ -374,12 +381,7 @@ extern "C" int ospr_generate_fresnel(const float* d_target, int H, int W, int N,
     if ((rc = device_tables(&tab))) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
     float2* chirp = reinterpret_cast<float2*>(static_cast<char*>(d_ws) + chirp_off);
-    {
-        Launch ln("fresnel_chirp", st);
-        const cudaError_t le = launch_pdl(k_fresnel_chirp, dim3(unsigned((H + W + 255) / 256)), dim3(256), 0, st, H,
-                                          W, kappa, chirp);
-        if ((rc = ln.done("fresnel_chirp launch", le))) return rc;
-    }
+    if ((rc = fresnel_chirp_build(H, W, kappa, chirp, st))) return rc;
     OsprArgs a;
     a.target = d_target;
     a.H = H;

@@ -41,6 +41,11 @@ __device__ __forceinline__ uint32_t draw_code(const PhaseSource& ps, const Subfr
     return 0u;
 }
 
+// Fresnel propagation's separable quadratic phase Q(y, x) = chirp[y] * chirp[H + x] with
+// chirp[i] = exp(i*pi*kappa*(i - n/2)^2), n = H for the first H entries and W for the W
+// after them; written on the stream (ospr.cu).
+int fresnel_chirp_build(int H, int W, double kappa, float2* d_chirp, cudaStream_t st);
+
 // Host: validates the table arguments of a call and fills a PhaseSource.
 inline int make_phase_source(const char* who, const uint8_t* d_codes, int64_t L, int levels,
                              uint64_t seed, int64_t start, int64_t stride, PhaseSource* ps) {

@@ -98,6 +98,10 @@ _SIGS = {
                               _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
                               _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                               _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "gs_iterate_fresnel": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
+                                      _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_double,
+                                      _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
+                                      _c.c_void_p, _c.c_size_t, _c.c_void_p]),
     "ws_net_create": (_c.c_int, [_c.POINTER(_c.c_void_p), _c.c_uint64, _c.c_int]),
     "ws_net_destroy": (_c.c_int, [_c.c_void_p]),
     "ws_net_param_count": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_int64)]),
@@ -345,6 +349,17 @@ def gs_iterate(d_target, H, W, iters, levels, d_init_phase, d_codes, L, lut_leve
         ws_bytes = d_ws.numel() * d_ws.element_size()
     return _call("gs_iterate", _ptr(d_target), H, W, iters, levels, _ptr(d_init_phase),
                  _ptr(d_codes), L, lut_levels, seed, start_index, precision,
+                 _ptr(d_phase_codes), _ptr(d_replay), _ptr(d_err), _ptr(d_state_in),
+                 _ptr(d_state_out), _ptr(d_ws), ws_bytes, _stream(stream, d_target))
+
+
+def gs_iterate_fresnel(d_target, H, W, iters, levels, d_init_phase, d_codes, L, lut_levels, seed,
+                       start_index, kappa, d_phase_codes, d_replay, d_err, d_state_in, d_state_out,
+                       d_ws, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("gs_iterate_fresnel", _ptr(d_target), H, W, iters, levels, _ptr(d_init_phase),
+                 _ptr(d_codes), L, lut_levels, seed, start_index, float(kappa),
                  _ptr(d_phase_codes), _ptr(d_replay), _ptr(d_err), _ptr(d_state_in),
                  _ptr(d_state_out), _ptr(d_ws), ws_bytes, _stream(stream, d_target))
 

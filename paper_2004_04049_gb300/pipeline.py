@@ -72,6 +72,22 @@ def gs(target, iters, levels=256, codes=None, L=0, lut_levels=256, seed=0, start
     return out
 
 
+def gs_fresnel(target, iters, kappa, levels=256, codes=None, L=0, lut_levels=256, seed=0, start=0,
+               init_phase=None, ws=None, stream=None):
+    """GS under Fresnel propagation; returns a dict with 'codes', 'replay' and 'err'."""
+    H, W = target.shape
+    dev = target.device
+    need = holo.gs_workspace_size(H, W, iters)
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, dev)
+    out = {"codes": torch.empty((H, W), dtype=torch.uint8, device=dev),
+           "replay": torch.empty((H, W), dtype=torch.float32, device=dev),
+           "err": torch.empty(iters, dtype=torch.float64, device=dev)}
+    holo.gs_iterate_fresnel(target, H, W, iters, levels, init_phase, codes, L, lut_levels, seed, start, kappa,
+                            out["codes"], out["replay"], out["err"], None, None, ws, ws.numel(), stream=stream)
+    return out
+
+
 def error(replay, target, mask=None, ws=None, out=None, stream=None):
     """Returns a float64 tensor [alpha, mse, nmse] on the device."""
     H, W = target.shape
