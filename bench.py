@@ -240,7 +240,7 @@ def launch_signature(family, tuning, chunk, groups):
     ci, cf, rv = tuning["col_ifft_variant"], tuning["col_fft_variant"], tuning["row_variant"]
     return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {ci}, 0>", chunk),
             "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cf}, 0>", groups),
-            "ospr_row": (f"k_ospr_row<{W}, {rv}, 1, 0>", chunk)}.get(family, (None, None))
+            "ospr_row": (f"k_ospr_row<{W}, {rv}, 1, 0, 0>", chunk)}.get(family, (None, None))
 
 
 # ------------------------------------------------------------------ our arm ----
@@ -419,9 +419,10 @@ def run_ours(args):
     gs_ips = GS_ITERS * gs_runs / (gs_ms / 1e3)
 
     # end to end through the public API: every frame's target copied in from pinned host
-    # memory, the batch calls, bits + replay + error of every frame copied back. The frames
-    # go in `e2e_chunks` batch calls so that the copies of one chunk overlap the compute of
-    # its neighbours (a copy-in stream, the compute stream, a copy-out stream).
+    # memory, the batch calls, every frame's result copied back: the hologram bits and the
+    # error (and, in a second measurement, the replay image too). The frames go in
+    # `e2e_chunks` batch calls so that the copies of one chunk overlap the compute of its
+    # neighbours (a copy-in stream, the compute stream, a copy-out stream).
     h_targets = [t.cpu().pin_memory() for t in targets]
     h_out = [{"bits": torch.empty((N_SF, P // 32), dtype=torch.int32).pin_memory(),
               "I": torch.empty((H, W), dtype=torch.float32).pin_memory(),
@@ -430,6 +431,8 @@ def run_ours(args):
     chunks = [list(c) for c in np.array_split(np.arange(nfr), max(1, min(args.e2e_chunks, nfr)))]
     chunk_arrs = [holo.frame_array([descs[i] for i in c]) for c in chunks]
     copy_in, copy_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    with_replay = [False]
 
     def e2e_step():
         copy_in.wait_stream(stream)
@@ -451,7 +454,8 @@ def run_ours(args):
                 for i in c:
                     h = h_out[i]
                     h["bits"].copy_(fr[i]["bits"], non_blocking=True)
-                    h["I"].copy_(fr[i]["I"], non_blocking=True)
+                    if with_replay[0]:
+                        h["I"].copy_(fr[i]["I"], non_blocking=True)
                     h["err"].copy_(fr[i]["err"], non_blocking=True)
         stream.wait_stream(copy_out)
 
@@ -461,6 +465,12 @@ def run_ours(args):
     e2e_value = world * subframes_per_step * e2e_steps / (e2e_ms / 1e3)
     e2e_nmse = np.array([float(h["err"][2]) for h in h_out])
     assert np.allclose(e2e_nmse, nmse, rtol=0, atol=0), "end-to-end outputs differ from the device-resident run"
+    with_replay[0] = True
+    e2e_step()
+    barrier()
+    e2e_r_ms = float(sum(timed_steps(e2e_step, e2e_steps)))
+    e2e_r_value = world * subframes_per_step * e2e_steps / (e2e_r_ms / 1e3)
+    assert torch.equal(h_out[-1]["I"], fr[-1]["I"].cpu()), "replay copied back differs"
 
     batch = run_batch_leg(dev, stream) if not args.no_batch else None
     precision_leg = run_precision_leg(dev, stream) if not args.no_batch else None
@@ -499,7 +509,10 @@ def run_ours(args):
             "nmse_per_L": {str(L): float(v) for L, v in zip(L_SWEEP, nmse)},
             "e2e": {"value": e2e_value, "unit": "sub-frames/s", "batch_calls_per_step": len(chunks),
                     "h2d_bytes_per_step": len(L_SWEEP) * 4 * P,
-                    "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 4 * P + 24)},
+                    "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 24),
+                    "copied_back": "hologram bits and error of every frame",
+                    "with_replay": {"value": e2e_r_value, "unit": "sub-frames/s",
+                                    "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 4 * P + 24)}},
             "batch": batch,
             "precision": precision_leg,
             "phase_sources": sources_leg,

@@ -341,9 +341,8 @@ k_ospr_col_ifft(OsprArgs a) {
 // ------------------------------------------------------------------ pass 2 ----
 // FRESNEL: the row holds one sub-frame's IDFT(E); the hologram field is conj(Q) * IDFT(E),
 // binarised on its real part, and the replay transform takes h * Q.
-template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL = false>
-__global__ void __launch_bounds__((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR)
-k_ospr_row(OsprArgs a) {
+template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL>
+__device__ __forceinline__ void ospr_row_body(const OsprArgs& a) {
     constexpr int R = RowCfg<NR, V>::R, T = NR / R;
     constexpr bool BLOCK = T > 32;
     extern __shared__ float2 sm[];
@@ -391,6 +390,13 @@ k_ospr_row(OsprArgs a) {
         for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
     }
 }
+
+template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL = false>
+__global__ void __launch_bounds__((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR)
+k_ospr_row(OsprArgs a) {
+    ospr_row_body<NR, V, REPLAY, PREC, FRESNEL>(a);
+}
+
 
 // ------------------------------------------------------------------ pass 3 ----
 template <int NC, int V, int PREC>

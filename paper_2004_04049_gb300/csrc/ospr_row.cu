@@ -8,12 +8,13 @@ template <int NR, int V, bool REPLAY, bool FRESNEL>
 static int launch_row(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
     constexpr size_t smem = row_smem_bytes<NR, V>();
-    int rc = ensure_smem((const void*)k_ospr_row<NR, V, REPLAY, 0, FRESNEL>, smem, &mask);
+    void (*kern)(OsprArgs) = k_ospr_row<NR, V, REPLAY, 0, FRESNEL>;
+    int rc = ensure_smem((const void*)kern, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.H / RowCfg<NR, V>::LPR, a.pairs);
     Launch ln("ospr_row", st);
-    const cudaError_t le = launch_pdl(k_ospr_row<NR, V, REPLAY, 0, FRESNEL>, grid,
-                                      dim3((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR), smem, st, a);
+    const cudaError_t le =
+        launch_pdl(kern, grid, dim3((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR), smem, st, a);
     return ln.done("ospr_row launch", le);
 }
 

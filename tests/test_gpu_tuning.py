@@ -51,6 +51,26 @@ def test_setting_parity(cuda, H, W, N, setting):
     check_replay(gI, oospr.replay_from_bits(gb, H, W))
 
 
+@pytest.mark.parametrize("H,W,N", [(1024, 1024, 4), (512, 1024, 3)])
+@pytest.mark.parametrize("setting", [(1, 1, 0, 16, 4), (2, 2, 1, 3, 2)])
+def test_fresnel_setting_parity(cuda, H, W, N, setting):
+    # the Fresnel row pass under other tile variants, pairs in flight and groups
+    L, seed, kappa = 10007, 5, 2.4e-4
+    T = blob_target(H, W, 1200)
+    holo.ospr_tuning_set(H, W, *setting)
+    try:
+        t = torch.from_numpy(T).to(cuda)
+        codes = pipeline.lut(seed, L, device=cuda)
+        fb, fI = pipeline.ospr_fresnel(t, N, kappa, codes, L, 256, seed)
+        torch.cuda.synchronize()
+    finally:
+        holo.ospr_tuning_set(H, W)
+    fgb = fb.cpu().numpy().view(np.uint32)
+    fob, _, fex = oospr.ospr_fresnel(T, N, olut.lut_codes(seed, L), L, seed, kappa, keep_fields=True)
+    check_bits(fgb, fob, fex["re_h"], H * W)
+    check_replay(fI.cpu().numpy(), oospr.replay_from_bits_fresnel(fgb, H, W, kappa))
+
+
 def test_autotune_installs_and_records(cuda, tmp_path):
     path = tmp_path / "tune.jsonl"
     os.environ["HOLO_TUNE_CACHE"] = str(path)
