@@ -4,7 +4,7 @@
 //
 // Two launches:
 //   partials1  per block: sum I*T^2, sum I^2, sum T^4, count
-//   partials2  every block first reduces partials1 to alpha (one warp, fixed order, so
+//   partials2  every warp first reduces partials1 to alpha (fixed order, so every warp of
 //              every block gets the same bits), then its share of sum (alpha I - T^2)^2;
 //              the block that finishes last (a completion counter, no waiting) adds the
 //              shares in block order and writes mse and nmse
@@ -109,7 +109,6 @@ k_err_pass2(const float* __restrict__ I, const float* __restrict__ T, const uint
             int64_t P, const ff* __restrict__ partials1, ff* partials2, unsigned* done,
             double* __restrict__ d_out) {
     __shared__ ff sm[32];
-    __shared__ float s_alpha;
     __shared__ bool s_last;
     pdl_wait();
     const int nb = gridDim.x;
@@ -118,20 +117,16 @@ k_err_pass2(const float* __restrict__ I, const float* __restrict__ T, const uint
     const bool vec = ((reinterpret_cast<uintptr_t>(I) | reinterpret_cast<uintptr_t>(T) |
                        reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
     const int64_t P4 = vec ? P / 4 : 0;
-    // first tile's loads go out before the wait for alpha
+    // first tile's loads go out before alpha is formed; every warp reduces the pass-1
+    // partials itself (same fixed order, so the same bits everywhere) instead of waiting
+    // at a block barrier for one warp to do it
     ErrTile x;
     err_load(I, T, tid, nth, P4, x);
-    if (threadIdx.x < 32) {
-        const ff s_it = warp_sum_array_ff(partials1, nb);
-        const ff s_ii = warp_sum_array_ff(partials1 + nb, nb);
-        const ff alpha = s_ii.hi > 0.f ? ff_div(s_it, s_ii) : ff_make(0.f);
-        if (threadIdx.x == 0) {
-            s_alpha = alpha.hi;
-            if (blockIdx.x == 0) d_out[0] = ff_to_double(alpha);
-        }
-    }
-    __syncthreads();
-    const float alpha = s_alpha;
+    const ff s_it = warp_sum_array_ff(partials1, nb);
+    const ff s_ii = warp_sum_array_ff(partials1 + nb, nb);
+    const ff alpha_ff = s_ii.hi > 0.f ? ff_div(s_it, s_ii) : ff_make(0.f);
+    if (blockIdx.x == 0 && threadIdx.x == 0) d_out[0] = ff_to_double(alpha_ff);
+    const float alpha = alpha_ff.hi;
     float acc[1] = {0.f};
     for (int64_t q0 = tid; q0 < P4; q0 += kErrVec * nth) {
         if (q0 != tid) err_load(I, T, q0, nth, P4, x);
