@@ -344,7 +344,6 @@ k_ospr_col_ifft(OsprArgs a) {
 template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL>
 __device__ __forceinline__ void ospr_row_body(const OsprArgs& a) {
     constexpr int R = RowCfg<NR, V>::R, T = NR / R;
-    constexpr bool BLOCK = T > 32;
     extern __shared__ float2 sm[];
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int lane = threadIdx.x & 31;
