@@ -318,7 +318,7 @@ def run_ours(args):
         return [a.elapsed_time(b) for a, b in times]
 
     # FFT tile variants and chunking for this shape, picked by the library's autotuner
-    tune_ms = holo.ospr_autotune(H, W, N_SF, reps=3, stream=s) if not args.no_tune else None
+    tune_ms = holo.ospr_autotune(H, W, N_SF, reps=5, stream=s) if not args.no_tune else None
     tuning = holo.ospr_tuning_get(H, W)
     ws = torch.empty(holo.ospr_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
     bws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=dev)
@@ -552,7 +552,7 @@ def run_batch_leg(dev, stream, reps=3):
     frames = batch_frames()
     tunings = {}
     for (H_, W_) in BATCH_SHAPES:
-        holo.ospr_autotune(H_, W_, 24, reps=2, stream=stream.cuda_stream)
+        holo.ospr_autotune(H_, W_, 24, reps=5, stream=stream.cuda_stream)
         tunings[f"{H_}x{W_}"] = holo.ospr_tuning_get(H_, W_)
     bufs = []
     descs = []
