@@ -839,7 +839,22 @@ def cpu_baseline_sample(seconds=15.0):
     return {"value": nall / dtp, "unit": "sub-frames/s", "cores": cores, "kind": "oracle",
             "sample": f"{nall} sub-frames of the 1024x1024 L=65536 frame, {per} per process on {cores} spawned "
                       f"processes (float64 numpy oracle), {dtp:.1f} s",
-            "single_core": single}
+            "single_core": single, "gs": _oracle_gs_rate()}
+
+
+def _oracle_gs_rate(iters=3):
+    """The oracle's GS at 1024x1024 (256 levels, LUT start L = 10007) on one core."""
+    from oracle import gs as ogs
+    from oracle import lut as olut
+    from synthetic import blob_target
+
+    T = blob_target(H, W, 1000)
+    table = olut.lut_codes(LUT_SEED, GS_L)
+    t0 = time.perf_counter()
+    ogs.gs(T, iters, table, GS_L, LUT_SEED)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": "iter/s", "cores": 1,
+            "sample": f"{iters} GS iterations at 1024x1024 (float64 numpy oracle, one process), {dt:.1f} s"}
 
 
 def run_reference(args):
