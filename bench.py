@@ -700,8 +700,21 @@ def run_fresnel_leg(dev, stream, reps=10, kappa=2.4e-4):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # per-pass launch times (CUDA events around every launch, outside the timed loop)
+    fams = ["fresnel_chirp", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize"]
+    holo.holo_profile_reset()
+    holo.holo_profile_enable(True)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize(dev)
+    holo.holo_profile_enable(False)
+    passes = {}
+    for f in fams:
+        n, t = holo.holo_profile_read(f)
+        passes[f] = {"launches_per_frame": n / 3, "us_per_launch": 1e3 * t / max(n, 1)}
     out = {"workload": f"1024x1024, N={N_SF}, L={GS_L}, kappa={kappa}", "ms_per_frame": ms,
-           "subframes_per_s": N_SF / (ms / 1e3), "energy_per_pixel": float(I.sum().item()) / P}
+           "subframes_per_s": N_SF / (ms / 1e3), "energy_per_pixel": float(I.sum().item()) / P,
+           "passes": passes}
     # GS under Fresnel propagation: 20 iterations from the LUT start, as the far-field GS leg
     gws = torch.empty(holo.gs_workspace_size(H, W, GS_ITERS), dtype=torch.uint8, device=dev)
     q = torch.empty((H, W), dtype=torch.uint8, device=dev)

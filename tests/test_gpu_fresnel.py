@@ -31,6 +31,8 @@ CASES = [
     (64, 4096, 2, 10007, 1e-4, "blob"),       # extreme aspect ratios
     (4096, 64, 2, 10007, 1e-4, "noise"),
     (1024, 1024, 2, 1048583, 2.4e-4, "blob"),   # the benchmark's frame size
+    (64, 64, 2, 1031, -0.01, "blob"),          # negative kappa (a converging wave)
+    (128, 64, 3, 4099, 0.75, "noise"),         # a chirp far beyond the sampling limit
 ]
 
 
