@@ -135,7 +135,7 @@ def kernel_bytes(family, P, pairs, groups, N):
         return pairs * 8 * P + groups * 4 * P
     if family == "ospr_finalize":
         return groups * 4 * P + 4 * P
-    if family in ("err_pass1", "err_pass2"):
+    if family == "replay_error":
         return 8 * P
     if family == "lut_build":
         return 0
@@ -350,8 +350,7 @@ def run_ours(args):
     seq_ms = timed_steps(step_sequential, args.steps, profile=True)
     seq_total = float(sum(seq_ms))
     seq_value = world * subframes_per_step * args.steps / (seq_total / 1e3)
-    fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "err_pass1",
-            "err_pass2"]
+    fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "replay_error"]
     prof = {f: holo.holo_profile_read(f) for f in fams}
     npairs = (N_SF + 1) // 2
     chunk = min(npairs, tuning["chunk"])

@@ -80,7 +80,7 @@ int holo_launch_count(uint64_t* out_count);
  * for the kernel family `name`, the number of launches and their summed duration in
  * milliseconds since the last holo_profile_reset. Families: "lut_build",
  * "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "fresnel_chirp", "gs_prepare",
- * "gs_col_init", "gs_row", "gs_col", "gs_finish", "err_pass1", "err_pass2", "lfsr_build",
+ * "gs_col_init", "gs_row", "gs_col", "gs_finish", "replay_error", "lfsr_build",
  * "nn_conv_fwd", "nn_conv_dgrad", "nn_conv_wgrad", "nn_elementwise",
  * "nn_loss", "nn_adam". */
 int holo_profile_enable(int on);
@@ -490,11 +490,15 @@ int replay_error_workspace_size(int H, int W, size_t* bytes);
  * with the intensity-domain, optimal-scale reading:
  *   alpha = sum(I*T^2) / sum(I^2);  mse = sum((alpha*I - T^2)^2) / P;
  *   nmse  = sum((alpha*I - T^2)^2) / sum(T^4)
- * Each thread sums a few pixels' terms in float32 (single-rounding fmaf); sums across
- * threads and blocks are float-float (about 48 significant bits) in a fixed order, so
- * results are bit-reproducible; only the three outputs are float64. Two launches (the
- * second one's last block to finish writes mse and nmse); the workspace holds the block
- * partial sums and a completion counter the first launch clears.
+ * One pass over the pixels: every block of 4096 pixels also forms its squared error at
+ * its own scale a_b and the sum of I*(a_b*I - T^2); the last block to finish reduces the
+ * blocks and writes alpha, mse and nmse through the exact identity
+ *   sum (alpha I - T^2)^2 = sum_b [S1_b + 2 (alpha - a_b) S2_b + (alpha - a_b)^2 sum_b I^2],
+ * whose terms do not cancel. Each thread sums its 16 pixels' terms in float32
+ * (single-rounding fmaf); sums across threads and blocks are float-float (about 48
+ * significant bits) in a fixed order, so results are bit-reproducible; only the three
+ * outputs are float64. The workspace holds the block partial sums and a completion
+ * counter that the call clears on the stream (cudaMemsetAsync) before its one launch.
  *
  *   d_replay  [H][W] float32 intensity I.   d_target [H][W] float32 amplitude T.
  *   d_mask    [H][W] uint8 or NULL: nonzero pixels are included (P = their count).

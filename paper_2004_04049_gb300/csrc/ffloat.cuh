@@ -45,6 +45,18 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
     return r;
 }
 
+// a * b: the product of the high parts formed exactly with an FMA (TwoProd), the cross
+// terms added in float32 (about 44 bits)
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    ff r;
+    quick_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
 // a / b with one Newton-style correction (about 44 bits)
 __device__ __forceinline__ ff ff_div(ff a, ff b) {
     const float q1 = __fdiv_rn(a.hi, b.hi);
@@ -72,15 +84,15 @@ __device__ __forceinline__ ff warp_sum_ff(ff v) {
     return v;
 }
 
-// K per-thread float32 sums -> K float-float block sums (valid in thread 0). Warps add in
-// float-float with a fixed butterfly; warp results are added in warp order. `sm` holds
-// >= 32*K ff values. blockDim.x must be a multiple of 32.
+// K per-thread float-float sums -> K float-float block sums (valid in thread 0). Warps add
+// with a fixed butterfly; warp results are added in warp order. `sm` holds >= 32*K ff
+// values. blockDim.x must be a multiple of 32.
 template <int K>
-__device__ __forceinline__ void block_sums_ff(const float (&v)[K], ff (&out)[K], ff* sm) {
+__device__ __forceinline__ void block_sums_ffv(const ff (&v)[K], ff (&out)[K], ff* sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ff w[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] = warp_sum_ff(ff_make(v[k]));
+    for (int k = 0; k < K; ++k) w[k] = warp_sum_ff(v[k]);
     __syncthreads();   // sm may still be read by a previous call
     if (lane == 0) {
 #pragma unroll
@@ -96,6 +108,15 @@ __device__ __forceinline__ void block_sums_ff(const float (&v)[K], ff (&out)[K],
             out[k] = acc;
         }
     }
+}
+
+// the same from K per-thread float32 sums
+template <int K>
+__device__ __forceinline__ void block_sums_ff(const float (&v)[K], ff (&out)[K], ff* sm) {
+    ff w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = ff_make(v[k]);
+    block_sums_ffv<K>(w, out, sm);
 }
 
 // float-float sum of x[0..n) by one warp: lane l adds x[l], x[l+32], ... in order, then

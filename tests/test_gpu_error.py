@@ -66,3 +66,20 @@ def test_exact_replay_zero_error_and_reproducible(cuda):
     assert np.array_equal(a, b)
     assert abs(a[0] - 0.5) < 1e-6
     assert a[2] < 1e-12
+
+
+def test_blocks_with_different_scales(cuda):
+    # the error is formed per block of 4096 pixels at the block's own scale and combined
+    # through an exact identity; blocks whose best scales differ widely (here 1, 3 and 0.2
+    # by region) and a near-exact fit inside each block exercise every term of it
+    rng = np.random.default_rng(5)
+    H, W = 512, 768
+    T = (0.2 + rng.random((H, W))).astype(np.float32)
+    scale = np.where(np.arange(H * W).reshape(H, W) // 4096 % 3 == 0, 1.0,
+                     np.where(np.arange(H * W).reshape(H, W) // 4096 % 3 == 1, 3.0, 0.2))
+    I = (scale * T.astype(np.float64) ** 2 * (1 + 1e-3 * rng.standard_normal((H, W)))).astype(np.float32)
+    g = pipeline.error(torch.from_numpy(I).to(cuda), torch.from_numpy(T).to(cuda)).cpu().numpy()
+    o = oerr.replay_error(I, T)
+    assert abs(g[0] - o[0]) <= 1e-6 * abs(o[0])
+    check_nmse(g[1], o[1])
+    check_nmse(g[2], o[2])
