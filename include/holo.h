@@ -185,7 +185,8 @@ int ospr_generate(const float* d_target, int H, int W, int N,
  * ospr_autotune times ospr_generate on synthetic data of this shape (a 10007-entry table)
  * for candidate settings (two sweeps of coordinate descent over the column IDFT variant,
  * row variant, column DFT variant, chunk and groups; each candidate the median of `reps`
- * runs after one warm-up, CUDA events on stream s), installs the fastest for this process
+ * runs after one warm-up, CUDA events on stream s; timings within 1% are a tie, won by the
+ * setting with the smaller workspace), installs the fastest for this process
  * and, when the environment variable HOLO_TUNE_CACHE names a file, writes every installed
  * setting there (one JSON object per line), from where later processes read it. It
  * allocates and frees its own scratch (HOLO_ENOMEM if that fails) and synchronises s.

@@ -495,12 +495,18 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
     float best_t = 0.f;
     if (!rc) rc = measure(best, &best_t);
     // coordinate descent, two sweeps: column IDFT tiles, row tiles, column DFT tiles,
-    // pairs in flight, accumulator groups (a tile choice can change the best chunking)
+    // pairs in flight, accumulator groups (a tile choice can change the best chunking).
+    // Timings within 1% count as a tie, won by the smaller workspace (fewer fields in
+    // flight or accumulators): it leaves more of L2 to frames running beside this one and
+    // gives the finalize fewer bytes to read.
     auto consider = [&](OsprTuning t) {
         if (rc) return;
         float ms = 0.f;
         rc = measure(t, &ms);
-        if (!rc && ms < best_t) { best_t = ms; best = t; }
+        if (rc) return;
+        const bool tie = ms <= best_t * 1.01f && ms >= best_t * 0.99f;
+        const bool smaller = ospr_plan_with(H, W, N, t).total < ospr_plan_with(H, W, N, best).total;
+        if ((!tie && ms < best_t) || (tie && smaller)) { best_t = ms; best = t; }
     };
     const int chunks[] = {2, 4, 8, 12, 16};
     const int groups[] = {1, 2, 4};
