@@ -24,6 +24,7 @@ import csv
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -185,7 +186,8 @@ def record_traffic(csv_path, command, out_path=TRAFFIC_FILE):
     for r in rows[hdr + 1:]:
         if len(r) <= vi:
             continue
-        name = r[ki].replace("void ", "").split("(")[0]
+        # "void holo::k_x<...>(holo::OsprArgs)" or "void k_x<...>(OsprArgs)", by ncu's mode
+        name = re.sub(r"^(\w+::)+", "", r[ki].replace("void ", "").split("(")[0])
         fam = KERNEL_FAMILY.get(name.split("<")[0])
         if fam is None:
             continue
