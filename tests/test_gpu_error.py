@@ -15,7 +15,9 @@ from parity import check_nmse
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("H,W", [(1024, 1024), (256, 256), (33, 17), (1, 5), (2048, 1024)])
+@pytest.mark.parametrize("H,W", [(1024, 1024), (256, 256), (33, 17), (1, 5), (2048, 1024),
+                                 (1000, 1001),      # odd pixel count: the scalar path over 245 blocks
+                                 (4096, 4096)])     # 4096 blocks: the last block loops over the partials
 def test_matches_oracle(cuda, H, W):
     rng = np.random.default_rng(H * 7 + W)
     T = rng.random((H, W)).astype(np.float32)
