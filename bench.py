@@ -1056,6 +1056,15 @@ def run_case(name):
             out = pipeline.gs(T, GS_ITERS, 256, codes, GS_L, 256, LUT_SEED)
         torch.cuda.synchronize()
         print("case gs ok, eps_20 / P", float(out["err"][-1]) / (H * W))
+    elif name == "fresnel":
+        # one 1024x1024 OSPR frame under Fresnel propagation (N=24, L=10007, kappa=2.4e-4), twice
+        from paper_2004_04049_gb300 import holo
+        T = torch.from_numpy(blob_target(H, W, 1000)).to(dev)
+        codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
+        for _ in range(2):
+            _, I = pipeline.ospr_fresnel(T, N_SF, 2.4e-4, codes, GS_L, 256, LUT_SEED)
+        torch.cuda.synchronize()
+        print("case fresnel ok, energy per pixel", float(I.sum()) / (H * W))
     elif name == "tc":
         # one 1024x1024 frame (N=24, L=10007) twice in float32, then twice in bf16x2
         from paper_2004_04049_gb300 import holo
