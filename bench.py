@@ -1058,7 +1058,6 @@ def run_case(name):
         print("case gs ok, eps_20 / P", float(out["err"][-1]) / (H * W))
     elif name == "fresnel":
         # one 1024x1024 OSPR frame under Fresnel propagation (N=24, L=10007, kappa=2.4e-4), twice
-        from paper_2004_04049_gb300 import holo
         T = torch.from_numpy(blob_target(H, W, 1000)).to(dev)
         codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
         for _ in range(2):
