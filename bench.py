@@ -335,11 +335,15 @@ def run_ours(args):
     step_ms = timed_steps(step_batch, args.steps)
     clocks = sampler.stop()
     launches = holo.holo_launch_count() - launches0
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
+    def max_over_ranks(ms):
+        """The slowest rank's time (every rank runs the same work)."""
+        if world == 1:
+            return ms
+        t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        return float(t.item())
+
+    total_ms = max_over_ranks(float(sum(step_ms)))
     subframes_per_step = nfr * N_SF
     value = world * subframes_per_step * args.steps / (total_ms / 1e3)
     nmse = np.array([float(f["err"][2].item()) for f in fr])
@@ -350,7 +354,7 @@ def run_ours(args):
         step_sequential()
     barrier()
     seq_ms = timed_steps(step_sequential, args.steps, profile=True)
-    seq_total = float(sum(seq_ms))
+    seq_total = max_over_ranks(float(sum(seq_ms)))
     seq_value = world * subframes_per_step * args.steps / (seq_total / 1e3)
     fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "replay_error"]
     prof = {f: holo.holo_profile_read(f) for f in fams}
@@ -462,14 +466,14 @@ def run_ours(args):
 
     e2e_step()
     barrier()
-    e2e_ms = float(sum(timed_steps(e2e_step, e2e_steps)))
+    e2e_ms = max_over_ranks(float(sum(timed_steps(e2e_step, e2e_steps))))
     e2e_value = world * subframes_per_step * e2e_steps / (e2e_ms / 1e3)
     e2e_nmse = np.array([float(h["err"][2]) for h in h_out])
     assert np.allclose(e2e_nmse, nmse, rtol=0, atol=0), "end-to-end outputs differ from the device-resident run"
     with_replay[0] = True
     e2e_step()
     barrier()
-    e2e_r_ms = float(sum(timed_steps(e2e_step, e2e_steps)))
+    e2e_r_ms = max_over_ranks(float(sum(timed_steps(e2e_step, e2e_steps))))
     e2e_r_value = world * subframes_per_step * e2e_steps / (e2e_r_ms / 1e3)
     assert torch.equal(h_out[-1]["I"], fr[-1]["I"].cpu()), "replay copied back differs"
 
