@@ -16,7 +16,9 @@
 // Each thread forms its terms with single-rounding fmaf in float32 over its 16 pixels;
 // every sum across threads, warps and blocks is float-float (about 48 significant bits,
 // ffloat.cuh) in a fixed order, so results are bit-reproducible, and only the three
-// reported values are converted to float64. HBM-bound: 8 bytes per pixel (+1 with a mask).
+// reported values are converted to float64. Reads 8 bytes per pixel once (+1 with a
+// mask); at 1024^2 the block reductions and the last block's combination, not the bytes,
+// take most of the time.
 #include "ffloat.cuh"
 #include "runtime.h"
 
