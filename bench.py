@@ -423,46 +423,27 @@ def run_ours(args):
     gs_nmse = float(gout[2].item())
     gs_ips = GS_ITERS * gs_runs / (gs_ms / 1e3)
 
-    # end to end through the public API: every frame's target copied in from pinned host
-    # memory, the batch calls, every frame's result copied back: the hologram bits and the
-    # error (and, in a second measurement, the replay image too). The frames go in
-    # `e2e_chunks` batch calls so that the copies of one chunk overlap the compute of its
-    # neighbours (a copy-in stream, the compute stream, a copy-out stream).
+    # end to end through the public API: every frame's target copied in from page-locked
+    # host memory and every frame's result copied back (the hologram bits and the error;
+    # in a second measurement the replay image too), all inside one
+    # ospr_generate_batch_host call, which issues each frame's copies on that frame's
+    # internal stream so that they overlap other frames' kernels.
     h_targets = [t.cpu().pin_memory() for t in targets]
     h_out = [{"bits": torch.empty((N_SF, P // 32), dtype=torch.int32).pin_memory(),
               "I": torch.empty((H, W), dtype=torch.float32).pin_memory(),
               "err": torch.empty(3, dtype=torch.float64).pin_memory()} for _ in fr]
     e2e_steps = max(1, min(args.steps, 10))
-    chunks = [list(c) for c in np.array_split(np.arange(nfr), max(1, min(args.e2e_chunks, nfr)))]
-    chunk_arrs = [holo.frame_array([descs[i] for i in c]) for c in chunks]
-    copy_in, copy_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
+    def host_table(replay):
+        return holo.frame_host_array([holo.frame_host(h_targets[i % 2], h_out[i]["bits"],
+                                                      h_out[i]["I"] if replay else None, h_out[i]["err"])
+                                      for i in range(nfr)])
+
+    hosts = {False: host_table(False), True: host_table(True)}
     with_replay = [False]
 
     def e2e_step():
-        copy_in.wait_stream(stream)
-        ev_in = []
-        for c in chunks:
-            with torch.cuda.stream(copy_in):
-                for i in c:
-                    fr[i]["T"].copy_(h_targets[i % 2], non_blocking=True)
-                e = torch.cuda.Event()
-                e.record(copy_in)
-                ev_in.append(e)
-        for c, a, e in zip(chunks, chunk_arrs, ev_in):
-            stream.wait_event(e)
-            holo.ospr_generate_batch(a, holo.HOLO_FP32, bws, stream=s)
-            done = torch.cuda.Event()
-            done.record(stream)
-            copy_out.wait_event(done)
-            with torch.cuda.stream(copy_out):
-                for i in c:
-                    h = h_out[i]
-                    h["bits"].copy_(fr[i]["bits"], non_blocking=True)
-                    if with_replay[0]:
-                        h["I"].copy_(fr[i]["I"], non_blocking=True)
-                    h["err"].copy_(fr[i]["err"], non_blocking=True)
-        stream.wait_stream(copy_out)
+        holo.ospr_generate_batch_host(arr, hosts[with_replay[0]], holo.HOLO_FP32, bws, stream=s)
 
     e2e_step()
     barrier()
@@ -512,7 +493,8 @@ def run_ours(args):
                    "bytes_per_iter_model": 36 * P,
                    "achieved_GBps": gs_ips * 36 * P / 1e9},
             "nmse_per_L": {str(L): float(v) for L, v in zip(L_SWEEP, nmse)},
-            "e2e": {"value": e2e_value, "unit": "sub-frames/s", "batch_calls_per_step": len(chunks),
+            "e2e": {"value": e2e_value, "unit": "sub-frames/s",
+                    "how": "one ospr_generate_batch_host call a step: host targets in, results out",
                     "h2d_bytes_per_step": len(L_SWEEP) * 4 * P,
                     "d2h_bytes_per_step": len(L_SWEEP) * (N_SF * P // 8 + 24),
                     "copied_back": "hologram bits and error of every frame",
@@ -1092,7 +1074,6 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-shape batch leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default FFT tiles and chunking")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--e2e-chunks", type=int, default=4, help="batch calls per end-to-end step (copy overlap)")
     ap.add_argument("--case", default=None, help="run a small fixed workload for a profiler capture")
     ap.add_argument("--learned", action="store_true", help="run the learned GS warm-start experiment")
     ap.add_argument("--learned-n", type=int, default=20000)

@@ -312,6 +312,34 @@ int ospr_generate_batch(const holo_frame_desc* h_frames, int n_frames, int preci
                         void* d_ws, size_t ws_bytes, holo_stream_t s);
 
 /*
+ * Host buffers of one batch frame for ospr_generate_batch_host (an engineering extension
+ * for callers whose targets arrive from and whose holograms go back to host memory). Each
+ * pointer is optional (NULL: no copy); sizes follow the frame's descriptor.
+ *   h_target     [H][W] float32, copied into the frame's d_target before its work.
+ *   h_holo_bits  [N][H*W/32] uint32, copied from d_holo_bits after the frame.
+ *   h_replay     [H][W] float32, copied from d_replay after the frame.
+ *   h_err        [3] float64, copied from d_err after the frame.
+ */
+typedef struct holo_frame_host {
+    const float* h_target;
+    uint32_t* h_holo_bits;
+    float* h_replay;
+    double* h_err;
+} holo_frame_host;
+
+/*
+ * ospr_generate_batch_host - ospr_generate_batch with each frame's host-to-device and
+ * device-to-host copies issued on that frame's internal stream around its work, so that
+ * one frame's copies overlap other frames' kernels. Page-locked host buffers make the
+ * copies asynchronous (pageable ones are copied synchronously by CUDA). The host buffers
+ * must stay valid, and untouched by the caller, until stream `s` passes the call. Frames
+ * must not share a d_target (each frame's copy writes it). HOLO_EINVAL for a NULL table
+ * or a host output whose device buffer is NULL; other errors as ospr_generate_batch.
+ */
+int ospr_generate_batch_host(const holo_frame_desc* h_frames, const holo_frame_host* h_io, int n_frames,
+                             int precision, void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/*
  * A CUDA graph of a whole batch: ospr_batch_graph_create runs the batch once on a private
  * stream (to finish every lazy set-up), then captures it into an executable graph, so
  * that one holo_graph_launch replays the whole batch with a single launch. The graph

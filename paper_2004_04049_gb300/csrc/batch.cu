@@ -106,8 +106,17 @@ static int plan_batch(const holo_frame_desc* f, int n, int precision, BatchPlan*
     return HOLO_OK;
 }
 
+// copies of one frame between host and device on that frame's internal stream
+static int frame_copy(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st, int i,
+                      const char* what) {
+    if (!dst || !src || !bytes) return HOLO_OK;
+    const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, st);
+    if (e != cudaSuccess) return fail(cuda_status(e, what), "batch frame %d: %s", i, holo_last_error());
+    return HOLO_OK;
+}
+
 static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws, size_t ws_bytes,
-                     cudaStream_t s, const BatchPlan& pl) {
+                     cudaStream_t s, const BatchPlan& pl, const holo_frame_host* io = nullptr) {
     if (!d_ws || ws_bytes < pl.total)
         return fail(HOLO_EWORKSPACE, "batch: workspace %zu bytes, need %zu", ws_bytes, pl.total);
     if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0)
@@ -125,6 +134,12 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
         const int k = pl.stream_of[i];
         char* slot = static_cast<char*>(d_ws) + size_t(k) * pl.slot_bytes;
         holo_stream_t hs = reinterpret_cast<holo_stream_t>(ds->st[k]);
+        const size_t P = size_t(d.H) * size_t(d.W);
+        if (io && (rc = frame_copy(const_cast<float*>(d.d_target), io[i].h_target, P * sizeof(float),
+                                   cudaMemcpyHostToDevice, ds->st[k], i, "batch: target copy"))) {
+            first_rc = rc;
+            break;
+        }
         if (d.build_lut && d.L > 0)
             if ((rc = lut_build(d.seed, d.L, d.levels, d.d_codes, nullptr, hs))) {
                 first_rc = fail(rc, "batch frame %d: %s", i, holo_last_error());
@@ -140,6 +155,18 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
                                           pl.slot_bytes - pl.err_off, hs))) {
             first_rc = fail(rc, "batch frame %d: %s", i, holo_last_error());
             break;
+        }
+        if (io) {
+            const size_t words = size_t(d.N) * (P / 32);
+            if ((rc = frame_copy(io[i].h_holo_bits, d.d_holo_bits, words * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                 ds->st[k], i, "batch: bits copy")) ||
+                (rc = frame_copy(io[i].h_replay, d.d_replay, P * sizeof(float), cudaMemcpyDeviceToHost, ds->st[k], i,
+                                 "batch: replay copy")) ||
+                (rc = frame_copy(io[i].h_err, d.d_err, 3 * sizeof(double), cudaMemcpyDeviceToHost, ds->st[k], i,
+                                 "batch: error copy"))) {
+                first_rc = rc;
+                break;
+            }
         }
     }
     // join every branch back to the caller's stream, also after an error, so that no
@@ -180,6 +207,23 @@ extern "C" int ospr_generate_batch(const holo_frame_desc* h_frames, int n_frames
     int rc = plan_batch(h_frames, n_frames, precision, &pl);
     if (rc) return rc;
     return run_batch(h_frames, n_frames, precision, d_ws, ws_bytes, reinterpret_cast<cudaStream_t>(s), pl);
+}
+
+extern "C" int ospr_generate_batch_host(const holo_frame_desc* h_frames, const holo_frame_host* h_io, int n_frames,
+                                        int precision, void* d_ws, size_t ws_bytes, holo_stream_t s) {
+    clear_error();
+    if (!h_io) return fail(HOLO_EINVAL, "ospr_generate_batch_host: NULL host buffer table");
+    BatchPlan pl;
+    int rc = plan_batch(h_frames, n_frames, precision, &pl);
+    if (rc) return rc;
+    for (int i = 0; i < n_frames; ++i) {
+        if (h_io[i].h_holo_bits && !h_frames[i].d_holo_bits)
+            return fail(HOLO_EINVAL, "batch frame %d: h_holo_bits without d_holo_bits", i);
+        if (h_io[i].h_replay && !h_frames[i].d_replay)
+            return fail(HOLO_EINVAL, "batch frame %d: h_replay without d_replay", i);
+        if (h_io[i].h_err && !h_frames[i].d_err) return fail(HOLO_EINVAL, "batch frame %d: h_err without d_err", i);
+    }
+    return run_batch(h_frames, n_frames, precision, d_ws, ws_bytes, reinterpret_cast<cudaStream_t>(s), pl, h_io);
 }
 
 extern "C" int ospr_batch_graph_create(const holo_frame_desc* h_frames, int n_frames, int precision,

@@ -58,6 +58,21 @@ def frame_desc(d_target, H, W, N, d_codes=None, L=0, levels=256, seed=0, build_l
 def frame_array(descs):
     arr = (FrameDesc * len(descs))(*descs)
     return arr
+
+
+class FrameHost(ctypes.Structure):
+    """holo_frame_host of include/holo.h: optional host buffers of one batch frame."""
+    _fields_ = [("h_target", ctypes.c_void_p), ("h_holo_bits", ctypes.c_void_p), ("h_replay", ctypes.c_void_p),
+                ("h_err", ctypes.c_void_p)]
+
+
+def frame_host(h_target=None, h_holo_bits=None, h_replay=None, h_err=None):
+    """Host tensors (page-locked for asynchronous copies) or addresses, each optional."""
+    return FrameHost(_ptr(h_target), _ptr(h_holo_bits), _ptr(h_replay), _ptr(h_err))
+
+
+def frame_host_array(hosts):
+    return (FrameHost * len(hosts))(*hosts)
 _SIGS = {
     "holo_version": (_c.c_int, []),
     "holo_last_error": (_c.c_char_p, []),
@@ -84,6 +99,8 @@ _SIGS = {
                                          _c.c_void_p, _c.c_void_p, _c.c_void_p]),
     "ospr_batch_workspace_size": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "ospr_generate_batch": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "ospr_generate_batch_host": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
+                                            _c.c_void_p]),
     "ospr_batch_graph_create": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
                                            _c.POINTER(_c.c_void_p)]),
     "holo_graph_launch": (_c.c_int, [_c.c_void_p, _c.c_void_p]),
@@ -279,6 +296,15 @@ def ospr_generate_batch(frames, precision, d_ws, ws_bytes=None, stream=None):
         ws_bytes = d_ws.numel() * d_ws.element_size()
     return _call("ospr_generate_batch", ctypes.cast(frames, ctypes.c_void_p), len(frames), precision,
                  _ptr(d_ws), ws_bytes, _stream(stream, d_ws))
+
+
+def ospr_generate_batch_host(frames, hosts, precision, d_ws, ws_bytes=None, stream=None):
+    if len(hosts) != len(frames):
+        raise ValueError("one host entry per frame")
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("ospr_generate_batch_host", ctypes.cast(frames, ctypes.c_void_p), ctypes.cast(hosts, ctypes.c_void_p),
+                 len(frames), precision, _ptr(d_ws), ws_bytes, _stream(stream, d_ws))
 
 
 def ospr_batch_graph_create(frames, precision, d_ws, ws_bytes=None):

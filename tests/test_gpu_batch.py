@@ -99,3 +99,37 @@ def test_batch_reports_bad_frame(cuda):
     with pytest.raises(holo.HoloError) as ei:
         holo.ospr_batch_workspace_size(arr)
     assert "frame 1" in str(ei.value)
+
+
+def test_batch_with_host_buffers(cuda):
+    # the same frames with their targets coming from and their results going back to
+    # page-locked host memory, the copies issued by the library around each frame
+    bufs = [_alloc(cuda, s, k) for k, s in enumerate(FRAMES)]
+    arr = _descs(bufs)
+    ws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=cuda)
+    holo.ospr_generate_batch(arr, holo.HOLO_FP32, ws)
+    torch.cuda.synchronize()
+    ref = [(b["bits"].cpu(), b["I"].cpu(), b["err"].cpu()) for b in bufs]
+    hosts, h = [], []
+    for b in bufs:
+        t = b["T"].cpu().pin_memory()
+        b["T"].zero_()                                  # the call must copy the target in
+        o = {"T": t, "bits": torch.zeros(b["bits"].shape, dtype=torch.int32).pin_memory(),
+             "I": torch.zeros(b["I"].shape, dtype=torch.float32).pin_memory(),
+             "err": torch.zeros(3, dtype=torch.float64).pin_memory()}
+        h.append(o)
+        hosts.append(holo.frame_host(o["T"], o["bits"], o["I"], o["err"]))
+    holo.ospr_generate_batch_host(arr, holo.frame_host_array(hosts), holo.HOLO_FP32, ws)
+    torch.cuda.synchronize()
+    for k, (o, r) in enumerate(zip(h, ref)):
+        assert torch.equal(o["bits"], r[0]), k
+        assert torch.equal(o["I"], r[1]), k
+        assert torch.equal(o["err"], r[2]), k
+    with pytest.raises(holo.HoloError) as ei:
+        bad = holo.frame_host_array([holo.frame_host(None, None, h[0]["I"], None)] +
+                                    [holo.frame_host() for _ in bufs[1:]])
+        nodev = holo.frame_array([holo.frame_desc(bufs[0]["T"], *FRAMES[0][:3], bufs[0]["codes"], FRAMES[0][3], 256,
+                                                  FRAMES[0][4], True, 0, 0, bufs[0]["bits"], None, None)] +
+                                 list(_descs(bufs))[1:])
+        holo.ospr_generate_batch_host(nodev, bad, holo.HOLO_FP32, ws)
+    assert ei.value.status == holo.HOLO_EINVAL
