@@ -138,24 +138,4 @@ __device__ __forceinline__ ff warp_sum_array_ff(const ff* __restrict__ x, int n)
     return warp_sum_ff(v);
 }
 
-// warp_sum_array_ff over values other blocks of the running kernel wrote (and fenced):
-// loads go through L2 (ld.global.cg), never through the non-coherent read-only path
-__device__ __forceinline__ ff warp_sum_array_ff_cg(const ff* x, int n) {
-    const int lane = threadIdx.x & 31;
-    const float2* x2 = reinterpret_cast<const float2*>(x);
-    ff v = ff_make(0.f);
-    for (int base = 0; base < n; base += 32 * 8) {
-        ff buf[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = base + 32 * k + lane;
-            const float2 q = i < n ? __ldcg(x2 + i) : make_float2(0.f, 0.f);
-            buf[k] = ff{q.x, q.y};
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v = ff_add(v, buf[k]);
-    }
-    return warp_sum_ff(v);
-}
-
 }  // namespace holo
