@@ -10,7 +10,8 @@
  *    H and W are powers of two in [64, 4096] unless a call says otherwise.
  *  - Every pointer named d_* is a device pointer on the current CUDA device. The caller
  *    owns all of them (inputs, outputs and the workspace) and keeps them alive until the
- *    stream has finished the call. The library never frees caller memory.
+ *    stream has finished the call. The library never frees caller memory. Pointers
+ *    named h_* are host pointers, with the same ownership rule.
  *  - Every call is asynchronous on the caller's stream `s` (NULL = the legacy default
  *    stream). The return value reports argument validation and launch errors only;
  *    errors raised while the kernels run surface at the next synchronisation and via
