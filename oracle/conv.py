@@ -126,3 +126,67 @@ def phase_loss_grad(out, z, wts, eps=1e-12):
     gu = v * (ga * v - gb * u) / r3
     gv = u * (gb * u - ga * v) / r3
     return np.stack([gu, gv], axis=-1)
+
+
+def bilinear_resample(x, Ho, Wo):
+    """Bilinear resampling of x [H, W] (float64) to Ho x Wo with half-pixel centres.
+
+    Output pixel (oy, ox) is centred at input coordinates
+        sy = (oy + 1/2) * H / Ho - 1/2,   sx = (ox + 1/2) * W / Wo - 1/2,
+    each clamped to [0, H - 1] and [0, W - 1] (the edge value is held beyond the outer
+    pixel centres). With y0 = floor(sy), y1 = min(y0 + 1, H - 1), fy = sy - y0 and the same
+    for x, the value is
+        (1-fy)(1-fx) x[y0,x0] + (1-fy) fx x[y0,x1] + fy (1-fx) x[y1,x0] + fy fx x[y1,x1].
+    At Ho = H, Wo = W every sample falls on an input centre (the identity).
+    """
+    x = np.asarray(x, np.float64)
+    H, W = x.shape
+
+    def axis(n_in, n_out):
+        s = np.clip((np.arange(n_out) + 0.5) * n_in / n_out - 0.5, 0.0, n_in - 1.0)
+        i0 = np.floor(s).astype(np.int64)
+        i1 = np.minimum(i0 + 1, n_in - 1)
+        return i0, i1, s - i0
+
+    y0, y1, fy = axis(H, Ho)
+    x0, x1, fx = axis(W, Wo)
+    fy = fy[:, None]
+    fx = fx[None, :]
+    return ((1 - fy) * (1 - fx) * x[np.ix_(y0, x0)] + (1 - fy) * fx * x[np.ix_(y0, x1)]
+            + fy * (1 - fx) * x[np.ix_(y1, x0)] + fy * fx * x[np.ix_(y1, x1)])
+
+
+def phase_of_uv(uv, Ho, Wo):
+    """The warm start's output phase at Ho x Wo: u and v (channels 0 and 1 of the head
+    output uv [H, W, C]) resampled bilinearly (``bilinear_resample``), then
+    phase = atan2(v, u) in (-pi, pi]. Resampling the phasor components rather than the
+    angle keeps the result continuous across the +-pi cut."""
+    uv = np.asarray(uv, np.float64)
+    u = bilinear_resample(uv[..., 0], Ho, Wo)
+    v = bilinear_resample(uv[..., 1], Ho, Wo)
+    return np.arctan2(v, u)
+
+
+def area_average(target, R):
+    """The network input: target [H, W] averaged over disjoint (H/R) x (W/R) blocks to R x R."""
+    t = np.asarray(target, np.float64)
+    H, W = t.shape
+    return t.reshape(R, H // R, R, W // R).mean(axis=(1, 3))
+
+
+def adam_step(w, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, 2015, Algorithm 1) at time step ``step`` >= 1.
+
+        m <- beta1 m + (1 - beta1) g;   v <- beta2 v + (1 - beta2) g^2
+        m_hat = m / (1 - beta1^step);   v_hat = v / (1 - beta2^step)
+        w <- w - lr * m_hat / (sqrt(v_hat) + eps)
+
+    Returns the new (w, m, v) as float64 arrays; the inputs are not modified.
+    """
+    w = np.asarray(w, np.float64)
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return w - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

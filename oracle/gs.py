@@ -73,6 +73,14 @@ def initial_field(target, table, L, seed, start=0, lut_levels=256, init_phase=No
     return Ts * np.exp(1j * theta)
 
 
+def replay_phase(E):
+    """The replay-plane phase of a GS state E (the warm start's training label): arg E in
+    (-pi, pi], with arg 0 := 0 as everywhere in GS."""
+    E = np.asarray(E, dtype=np.complex128)
+    ang = np.arctan2(E.imag, E.real)
+    return np.where((E.real == 0) & (E.imag == 0), 0.0, ang)
+
+
 def gs_step(E, Ts, levels=256):
     """One GS iteration from replay-plane field E. Returns (q, R, eps, E_next)."""
     Hf = _fft.ifft2(E)
