@@ -21,6 +21,9 @@
  *    from holo_last_error() on the same host thread.
  *  - There is no CPU fallback: without a usable CUDA device every compute call fails
  *    with HOLO_ECUDA.
+ *  - The library sets up per-device state on first use (constant tables, internal
+ *    streams, scratch addresses) and keeps it until the process exits; a process that
+ *    calls cudaDeviceReset must not call the library on that device afterwards.
  *  - Transforms are the unitary DFT of Eq. 1 (forward, exp(-2 pi i ...)) and Eq. 2
  *    (inverse, exp(+2 pi i ...)), scale 1/sqrt(H*W).
  */
@@ -225,6 +228,10 @@ int ospr_tuning_set(int H, int W, int col_ifft_variant, int col_fft_variant, int
  * writes every scratch byte before reading it, so no clearing is needed, but calls
  * whose kernels overlap on the GPU (different streams, or host threads) race on the
  * array and corrupt each other's results: serialise them.
+ * The looked-up address is kept for the life of the process, like the library's other
+ * per-device state (constant tables, internal streams): after a cudaDeviceReset the
+ * process must not call the library on that device again.
+ * Design-rule warnings (Section 8) are recorded as ospr_generate records them.
  * Errors: as ospr_generate, with HOLO_EWORKSPACE for shapes beyond the scratch.
  */
 #define HOLO_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
@@ -306,6 +313,10 @@ int ospr_batch_workspace_size(const holo_frame_desc* h_frames, int n_frames, int
  * each stream's frames run in order on that stream's slice of the workspace. The call
  * forks from and joins back to stream `s`: work queued on `s` before the call runs first,
  * work queued after it waits for every frame. Results equal those of per-frame calls.
+ * Calls may come from several host threads: a per-device lock is held while a call
+ * enqueues its work (fork to join), so concurrent calls queue one after the other on the
+ * internal streams, and an eager call made while another thread captures a batch graph
+ * waits for the capture to end.
  *   h_frames   host array of n_frames descriptors (read during the call only).
  * Errors: as the per-frame calls, with the index of the offending frame in the message.
  */
@@ -407,6 +418,17 @@ int gs_iterate_fresnel(const float* d_target, int H, int W, int iters, int level
                        void* d_ws, size_t ws_bytes, holo_stream_t s);
 
 /*
+ * gs_state_phase - the replay-plane phase of a GS state (Section 2: GS keeps the phase of
+ * the replay field and resets its amplitude to the target): d_phase[p] = arg(E_p) in
+ * (-pi, pi] with arg(0) = 0, E = d_state (the [H][W][2] float32 (re, im) field that
+ * gs_iterate writes to d_state_out). It is the label the warm-start network is trained
+ * on (the phase GS reached after its iterations). One elementwise launch on s; d_phase
+ * [H][W] float32 is caller-owned. 1 <= H*W <= 2^28, any H and W. Errors: HOLO_EINVAL,
+ * HOLO_ECUDA.
+ */
+int gs_state_phase(const float* d_state, int H, int W, float* d_phase, holo_stream_t s);
+
+/*
  * GS tile variants per shape (an engineering choice, not part of the method): the column
  * passes and the row pass each have variants 0..2 for line lengths 512..2048 (variant 0
  * only for other lengths; other values fall back to 0). Every variant computes the same
@@ -468,6 +490,30 @@ int ws_layer_shape(int layer, int* cin, int* cout, int* resolution);
 int ws_get_activation(const ws_net* net, const char* name, int batch, float* h_out, int64_t count);
 int ws_save(const ws_net* net, const char* path);
 int ws_load(ws_net* net, const char* path);
+
+/*
+ * ws_phase_resample - the last step of ws_infer on its own: the network's head output
+ * d_uv [H][W][channels] float32 (u in channel 0, v in channel 1; channels >= 2 is the
+ * pixel stride) is resampled bilinearly to Ho x Wo and d_phase [Ho][Wo] float32 receives
+ * atan2(v, u) in (-pi, pi]. Sampling: output (oy, ox) sits at input coordinates
+ * sy = (oy + 1/2)*H/Ho - 1/2, sx = (ox + 1/2)*W/Wo - 1/2, clamped to [0, H-1] and [0, W-1];
+ * the four neighbours floor(s) and min(floor(s) + 1, size - 1) are weighted by the
+ * fractional parts. Any sizes (non-integer scales included) with H*W*channels <= 2^31 and
+ * Ho*Wo <= 2^31. One launch on s; caller-owned buffers. Not in the paper: it maps the
+ * learned start onto gs_iterate's grid. Errors: HOLO_EINVAL, HOLO_ECUDA.
+ *
+ * ws_adam_update - the optimizer step ws_train_step applies to every parameter tensor
+ * (Kingma and Ba, 2015, Algorithm 1) on caller buffers of n float32 values:
+ *   m = beta1*m + (1-beta1)*g;  v = beta2*v + (1-beta2)*g^2;
+ *   w -= lr * (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps)
+ * in place on d_w, d_m, d_v; d_g is read. step >= 1 is the update's 1-based count,
+ * 0 <= beta1, beta2 < 1, eps >= 0, 1 <= n <= 2^31. One launch on s. Errors: HOLO_EINVAL,
+ * HOLO_ECUDA.
+ */
+int ws_phase_resample(const float* d_uv, int channels, int H, int W, int Ho, int Wo, float* d_phase,
+                      holo_stream_t s);
+int ws_adam_update(float* d_w, const float* d_g, float* d_m, float* d_v, int64_t n, float lr, float beta1,
+                   float beta2, float eps, int step, holo_stream_t s);
 
 /*
  * nn_conv3x3 - the network's convolution kernel on its own (3x3, zero padding 1, stride

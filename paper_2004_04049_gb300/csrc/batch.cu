@@ -27,12 +27,16 @@ static int batch_stream_count() {
     return n;
 }
 
-// internal streams and fork/join events, created once per device
+// internal streams and fork/join events, created once per device; `run_mu` serialises
+// the enqueue section of batch calls on the device (fork record to join wait), so that
+// calls from several host threads, or an eager call during another thread's graph
+// capture, never interleave their work on the shared streams and events
 struct DeviceStreams {
     cudaStream_t st[kMaxBatchStreams];
     cudaEvent_t fork;
     cudaEvent_t join[kMaxBatchStreams];
     bool ready = false;
+    std::mutex run_mu;
 };
 static std::mutex g_streams_mu;
 static DeviceStreams g_streams[64];
@@ -124,6 +128,7 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
     DeviceStreams* ds = nullptr;
     int rc = device_streams(&ds);
     if (rc) return rc;
+    std::lock_guard<std::mutex> run_lock(ds->run_mu);
     cudaError_t e = cudaEventRecord(ds->fork, s);
     if (e != cudaSuccess) return cuda_status(e, "batch: fork record");
     for (int k = 0; k < pl.streams; ++k)

@@ -527,6 +527,31 @@ extern "C" int gs_iterate_fresnel(const float* d_target, int H, int W, int iters
                            d_state_in, d_state_out, d_ws, ws_bytes, s);
 }
 
+namespace holo {
+
+// phase[p] = arg(state[p]) in (-pi, pi], with arg(0) = 0 whatever the zeros' signs
+__global__ void k_gs_state_phase(const float2* __restrict__ state, int64_t n, float* __restrict__ phase) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const float2 e = state[i];
+        phase[i] = (e.x == 0.f && e.y == 0.f) ? 0.f : atan2f(e.y, e.x);
+    }
+}
+
+}  // namespace holo
+
+extern "C" int gs_state_phase(const float* d_state, int H, int W, float* d_phase, holo_stream_t s) {
+    clear_error();
+    if (!d_state || !d_phase || H < 1 || W < 1 || int64_t(H) * W > (int64_t(1) << 28))
+        return fail(HOLO_EINVAL, "gs_state_phase: bad arguments (%dx%d)", H, W);
+    const int64_t n = int64_t(H) * W;
+    const int threads = 256;
+    const int blocks = int((n + threads - 1) / threads < 152 * 16 ? (n + threads - 1) / threads : 152 * 16);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    Launch ln("gs_state_phase", st);
+    k_gs_state_phase<<<blocks, threads, 0, st>>>(reinterpret_cast<const float2*>(d_state), n, d_phase);
+    return ln.done("gs_state_phase launch");
+}
+
 extern "C" int gs_tuning_set(int H, int W, int col_variant, int row_variant) {
     clear_error();
     int rc = gs_check_shape("gs_tuning_set", H, W);

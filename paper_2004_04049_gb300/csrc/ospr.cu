@@ -277,6 +277,19 @@ extern "C" int ospr_workspace_size(int H, int W, int N, int precision, size_t* b
     return HOLO_OK;
 }
 
+namespace holo {
+
+// Section 8 design rules for the table length (prime, longer than the sub-frame count
+// and than the largest image dimension): recorded as warnings with HOLO_OK
+static void ospr_design_rules(int64_t L, int N, int H, int W) {
+    if (L <= 0) return;
+    if (!is_prime(L)) warn("design rule: L=%lld is not prime", (long long)L);
+    if (L <= N) warn("design rule: L=%lld is not greater than N=%d", (long long)L, N);
+    if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
+}
+
+}  // namespace holo
+
 extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
                              const uint8_t* d_codes, int64_t L, int levels, uint64_t seed,
                              int64_t start_index, int64_t subframe_stride, int precision,
@@ -323,12 +336,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.fresnel = 0;
     a.chirp_y = a.chirp_x = nullptr;
     if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
-    // Section 8 design rules: warnings only
-    if (L > 0) {
-        if (!is_prime(L)) warn("design rule: L=%lld is not prime", (long long)L);
-        if (L <= N) warn("design rule: L=%lld is not greater than N=%d", (long long)L, N);
-        if (L <= (H > W ? H : W)) warn("design rule: L=%lld is not greater than max(H, W)", (long long)L);
-    }
+    ospr_design_rules(L, N, H, W);
     return HOLO_OK;
 }
 
@@ -636,5 +644,7 @@ extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
     a.chirp_y = a.chirp_x = nullptr;
     // every scratch byte a kernel reads was written earlier in this call (the first chunk
     // overwrites the accumulator), so nothing needs clearing between calls
-    return ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s));
+    if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
+    ospr_design_rules(L, N, H, W);
+    return HOLO_OK;
 }

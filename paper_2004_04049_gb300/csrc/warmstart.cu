@@ -427,6 +427,26 @@ extern "C" int ws_infer(ws_net* net, const float* d_target, int H, int W, float*
     return phase_out(net->out_f32, 8, kRes, kRes, H, W, d_phase_out, st);
 }
 
+extern "C" int ws_phase_resample(const float* d_uv, int channels, int H, int W, int Ho, int Wo, float* d_phase,
+                                 holo_stream_t s) {
+    clear_error();
+    if (!d_uv || !d_phase || channels < 2 || H < 1 || W < 1 || Ho < 1 || Wo < 1 ||
+        int64_t(H) * W * channels > (int64_t(1) << 31) || int64_t(Ho) * Wo > (int64_t(1) << 31))
+        return fail(HOLO_EINVAL, "ws_phase_resample: bad arguments (%d channels, %dx%d -> %dx%d)", channels, H, W,
+                    Ho, Wo);
+    return phase_out(d_uv, channels, H, W, Ho, Wo, d_phase, reinterpret_cast<cudaStream_t>(s));
+}
+
+extern "C" int ws_adam_update(float* d_w, const float* d_g, float* d_m, float* d_v, int64_t n, float lr, float beta1,
+                              float beta2, float eps, int step, holo_stream_t s) {
+    clear_error();
+    if (!d_w || !d_g || !d_m || !d_v || n < 1 || n > (int64_t(1) << 31) || step < 1 ||
+        !(beta1 >= 0.f && beta1 < 1.f) ||
+        !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))
+        return fail(HOLO_EINVAL, "ws_adam_update: bad arguments (n %lld, step %d)", (long long)n, step);
+    return adam(d_w, d_g, d_m, d_v, size_t(n), lr, beta1, beta2, eps, step, reinterpret_cast<cudaStream_t>(s));
+}
+
 // which: 0 weights [Cout][3][3][Cin], 1 biases [Cout], 2 weight gradients, 3 bias gradients
 extern "C" int ws_get_tensor(const ws_net* net, int layer, int which, float* h_out, int64_t count) {
     clear_error();

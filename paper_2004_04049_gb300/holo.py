@@ -119,6 +119,11 @@ _SIGS = {
                                       _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_double,
                                       _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                                       _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "gs_state_phase": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_void_p]),
+    "ws_phase_resample": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
+                                     _c.c_void_p]),
+    "ws_adam_update": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int64, _c.c_float,
+                                  _c.c_float, _c.c_float, _c.c_float, _c.c_int, _c.c_void_p]),
     "ws_net_create": (_c.c_int, [_c.POINTER(_c.c_void_p), _c.c_uint64, _c.c_int]),
     "ws_net_destroy": (_c.c_int, [_c.c_void_p]),
     "ws_net_param_count": (_c.c_int, [_c.c_void_p, _c.POINTER(_c.c_int64)]),
@@ -390,6 +395,10 @@ def gs_iterate_fresnel(d_target, H, W, iters, levels, d_init_phase, d_codes, L, 
                  _ptr(d_state_out), _ptr(d_ws), ws_bytes, _stream(stream, d_target))
 
 
+def gs_state_phase(d_state, H, W, d_phase, stream=None):
+    return _call("gs_state_phase", _ptr(d_state), H, W, _ptr(d_phase), _stream(stream, d_state))
+
+
 def replay_error_workspace_size(H, W):
     b = ctypes.c_size_t(0)
     _call("replay_error_workspace_size", H, W, ctypes.byref(b))
@@ -432,6 +441,15 @@ def ws_forward_backward(net, d_targets, d_label_phase, batch, d_loss=None, strea
 
 def ws_infer(net, d_target, H, W, d_phase_out, stream=None):
     return _call("ws_infer", net, _ptr(d_target), H, W, _ptr(d_phase_out), _stream(stream, d_target))
+
+
+def ws_phase_resample(d_uv, channels, H, W, Ho, Wo, d_phase, stream=None):
+    return _call("ws_phase_resample", _ptr(d_uv), channels, H, W, Ho, Wo, _ptr(d_phase), _stream(stream, d_uv))
+
+
+def ws_adam_update(d_w, d_g, d_m, d_v, n, lr, beta1, beta2, eps, step, stream=None):
+    return _call("ws_adam_update", _ptr(d_w), _ptr(d_g), _ptr(d_m), _ptr(d_v), n, lr, beta1, beta2, eps, step,
+                 _stream(stream, d_w))
 
 
 def ws_layer_shape(layer):

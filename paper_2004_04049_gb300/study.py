@@ -59,6 +59,12 @@ def prime_grid(S, N, points=40):
     return sorted(grid)
 
 
+def _sample_std(v):
+    """Sample standard deviation (n - 1 in the denominator); None for fewer than two samples,
+    where it is undefined."""
+    return float(np.std(v, ddof=1)) if np.size(v) > 1 else None
+
+
 def lut_length_study(sizes=(256, 128, 64), N=24, runs=100, n_targets=6, points=40, chunk_bytes=1 << 30,
                      device="cuda", log=None):
     from synthetic import blob_target, noise_target
@@ -104,13 +110,14 @@ def lut_length_study(sizes=(256, 128, 64), N=24, runs=100, n_targets=6, points=4
         rows = []
         for li, L in enumerate(Ls):
             v = ratio[li].ravel()
-            rows.append({"L": L, "mean": float(v.mean()), "std": float(v.std(ddof=1)),
+            rows.append({"L": L, "mean": float(v.mean()), "std": _sample_std(v),
                          "per_target": [float(x) for x in ratio[li].mean(axis=1)]})
         out[f"{S}x{S}"] = {"N": N, "runs": runs, "targets": n_targets,
                            "unrepeated_nmse": [float(x) for x in ref],
-                           "unrepeated_ratio_std": float((nmse[0] / ref[:, None]).std(ddof=1)),
+                           "unrepeated_ratio_std": _sample_std((nmse[0] / ref[:, None]).ravel()),
                            "rows": rows}
         if log:
             r10007 = next(r for r in rows if r["L"] == 10007)
-            log(f"{S}x{S}: {len(frames)} frames, L=10007 ratio {r10007['mean']:.4f} +- {2 * r10007['std']:.4f}")
+            spread = "" if r10007["std"] is None else f" +- {2 * r10007['std']:.4f}"
+            log(f"{S}x{S}: {len(frames)} frames, L=10007 ratio {r10007['mean']:.4f}{spread}")
     return out

@@ -31,7 +31,7 @@ def make_dataset(targets, iters=100, L=10007, seed=7, levels=256, stream=None):
     for i in range(n):
         holo.gs_iterate(targets[i], RES, RES, iters, levels, None, codes, L, 256, seed, 0, holo.HOLO_FP32,
                         None, None, err, None, state, ws, stream=stream)
-        labels[i] = torch.atan2(state[..., 1], state[..., 0])
+        holo.gs_state_phase(state, RES, RES, labels[i], stream=stream)
     return labels
 
 

@@ -133,3 +133,39 @@ def test_batch_with_host_buffers(cuda):
                                  list(_descs(bufs))[1:])
         holo.ospr_generate_batch_host(nodev, bad, holo.HOLO_FP32, ws)
     assert ei.value.status == holo.HOLO_EINVAL
+
+
+def test_batch_calls_from_two_threads(cuda):
+    # two host threads issue batch calls at the same time, each on its own stream with its
+    # own frames and workspace; the calls share the library's internal streams and events,
+    # so they must not interleave their forks and joins: each thread's results equal the
+    # per-frame results
+    import threading
+
+    sets = []
+    for r in range(2):
+        bufs = [_alloc(cuda, s, k + 10 * r) for k, s in enumerate(FRAMES)]
+        arr = _descs(bufs)
+        ws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=cuda)
+        sets.append((bufs, arr, ws, torch.cuda.Stream(cuda)))
+    torch.cuda.synchronize()
+    errors = []
+
+    def work(bufs, arr, ws, st):
+        try:
+            torch.cuda.set_device(cuda)
+            for _ in range(3):
+                holo.ospr_generate_batch(arr, holo.HOLO_FP32, ws, stream=st)
+            st.synchronize()
+        except Exception as e:   # reported after the join
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=s) for s in sets]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    torch.cuda.synchronize()
+    for bufs, _, _, _ in sets:
+        _check(bufs, _per_frame(cuda, bufs))

@@ -85,3 +85,23 @@ def test_blocks_with_different_scales(cuda):
     assert abs(g[0] - o[0]) <= 1e-6 * abs(o[0])
     check_nmse(g[1], o[1])
     check_nmse(g[2], o[2])
+
+
+def test_bright_half_and_dark_noise_half(cuda):
+    # half the frame a bright blob replayed faithfully, the other half a near-zero target
+    # under replay noise: the dark blocks' own scales a_b are far from the global alpha
+    # (|alpha - a_b| of the order of alpha), so the correction terms 2(alpha - a_b) S2_b and
+    # (alpha - a_b)^2 sum_b I^2 carry most of the squared error there
+    from synthetic import blob_target
+    rng = np.random.default_rng(6)
+    H, W = 1024, 1024
+    T = blob_target(H, W, 777).astype(np.float64)
+    T[H // 2:, :] = 1e-3 * rng.random((H // 2, W))
+    I = T ** 2 * (1 + 0.05 * rng.standard_normal((H, W)))
+    I[H // 2:, :] = 1e-4 * rng.random((H // 2, W))
+    T, I = T.astype(np.float32), np.abs(I).astype(np.float32)
+    g = pipeline.error(torch.from_numpy(I).to(cuda), torch.from_numpy(T).to(cuda)).cpu().numpy()
+    o = oerr.replay_error(I, T)
+    assert abs(g[0] - o[0]) <= 1e-6 * abs(o[0])
+    check_nmse(g[1], o[1])
+    check_nmse(g[2], o[2])
