@@ -347,16 +347,38 @@ int pack_weights(const float* w, int Cout, int Cin, __nv_bfloat16* wmat, __nv_bf
 }
 
 // --------------------------------------------------------------- output ----
+// Sample position of output index o (of n_out) on an input axis of n_in pixels, half-pixel
+// centres: s = (o + 1/2) n_in / n_out - 1/2 = ((2o + 1) n_in - n_out) / (2 n_out), clamped
+// to [0, n_in - 1]. The neighbour i0 = floor(s) is exact (integer division) and the
+// fraction f = s - i0 is one float division of exact integers.
+__device__ __forceinline__ void sample_axis(int o, int n_in, int n_out, int& i0, int& i1, float& f) {
+    const int64_t num = (2 * int64_t(o) + 1) * n_in - n_out;
+    const int64_t den = 2 * int64_t(n_out);
+    if (num <= 0) {
+        i0 = 0;
+        f = 0.f;
+    } else {
+        const int64_t q = num / den;
+        if (q >= n_in - 1) {
+            i0 = n_in - 1;
+            f = 0.f;
+        } else {
+            i0 = int(q);
+            f = float(num - q * den) / float(den);
+        }
+    }
+    i1 = i0 + 1 < n_in ? i0 + 1 : i0;
+}
+
 __global__ void k_phase_out(const float* __restrict__ out, int C, int H, int W, int Ho, int Wo,
                             float* __restrict__ phase) {
     const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= size_t(Ho) * Wo) return;
     const int oy = int(i / Wo), ox = int(i % Wo);
-    const float sy = fminf(fmaxf((oy + 0.5f) * float(H) / float(Ho) - 0.5f, 0.f), float(H - 1));
-    const float sx = fminf(fmaxf((ox + 0.5f) * float(W) / float(Wo) - 0.5f, 0.f), float(W - 1));
-    const int y0 = int(sy), x0 = int(sx);
-    const int y1 = y0 + 1 < H ? y0 + 1 : y0, x1 = x0 + 1 < W ? x0 + 1 : x0;
-    const float fy = sy - float(y0), fx = sx - float(x0);
+    int y0, y1, x0, x1;
+    float fy, fx;
+    sample_axis(oy, H, Ho, y0, y1, fy);
+    sample_axis(ox, W, Wo, x0, x1, fx);
     float u = 0.f, v = 0.f;
     const int ys[2] = {y0, y1}, xs[2] = {x0, x1};
     const float wy[2] = {1.f - fy, fy}, wx[2] = {1.f - fx, fx};

@@ -22,13 +22,14 @@ def _wrapped(d):
 
 def _check_phase(gpu_phase, uv64, Ho, Wo):
     """Element-wise: |GPU - oracle| (wrapped to (-pi, pi]) within 1e-5 rad plus the float32
-    rounding of the interpolation, which grows as 1/|(u, v)| where the neighbours cancel."""
+    rounding of the interpolation (weights and sums, relative 2^-24 each, of values up to
+    M = max |u|, |v|), which grows as M/|(u, v)| where the neighbours cancel."""
     ref = oc.phase_of_uv(uv64, Ho, Wo)
     u = oc.bilinear_resample(uv64[..., 0], Ho, Wo)
     v = oc.bilinear_resample(uv64[..., 1], Ho, Wo)
-    scale = oc.bilinear_resample(np.abs(uv64[..., 0]), Ho, Wo) + oc.bilinear_resample(np.abs(uv64[..., 1]), Ho, Wo)
+    M = np.abs(uv64[..., :2]).max()
     mag = np.hypot(u, v)
-    tol = 1e-5 + 4e-7 * scale / np.maximum(mag, 1e-30)
+    tol = 1e-5 + 1e-6 * M / np.maximum(mag, 1e-30)
     err = _wrapped(gpu_phase.astype(np.float64) - ref)
     bad = err > tol
     assert not bad.any(), (int(bad.sum()), float(err.max()))
