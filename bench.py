@@ -130,12 +130,10 @@ def kernel_bytes(family, P, pairs, groups, N):
     """Algorithmic HBM bytes of one launch (unique bytes the kernel must read and write)."""
     if family == "ospr_row":
         return pairs * (16 * P + 2 * P // 8)
-    if family in ("ospr_col_ifft", "ospr_row_gen"):
+    if family == "ospr_col_ifft":
         return 4 * P + pairs * 8 * P + min(2 * pairs * P, 1 << 20)
-    if family in ("ospr_col_fft", "ospr_row_acc"):
+    if family == "ospr_col_fft":
         return pairs * 8 * P + groups * 4 * P
-    if family == "ospr_bits_transpose":
-        return 2 * N * P // 8
     if family == "ospr_finalize":
         return groups * 4 * P + 4 * P
     if family == "replay_error":
@@ -164,13 +162,9 @@ KERNEL_SOURCES = {
     "ospr_col_fft": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_col.cu", "tc_dft.cuh"],
     "ospr_row": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_row.cu", "tc_dft.cuh"],
     "ospr_finalize": ["ospr.cu"],
-    "ospr_row_gen": ["ospr_rowfirst.cu", "ospr_kernels.cuh", "fft_core.cuh", "phase_source.cuh"],
-    "ospr_row_acc": ["ospr_rowfirst.cu", "ospr_kernels.cuh", "fft_core.cuh"],
-    "ospr_bits_transpose": ["ospr_rowfirst.cu"],
 }
 KERNEL_FAMILY = {"k_ospr_col_ifft": "ospr_col_ifft", "k_ospr_col_fft": "ospr_col_fft", "k_ospr_row": "ospr_row",
-                 "k_ospr_finalize": "ospr_finalize", "k_ospr_row_gen": "ospr_row_gen",
-                 "k_ospr_row_acc": "ospr_row_acc", "k_bits_transpose": "ospr_bits_transpose"}
+                 "k_ospr_finalize": "ospr_finalize"}
 
 
 def sources_digest(family):
@@ -244,13 +238,8 @@ def measured_instructions(family, kernel, grid_y):
 
 
 def launch_signature(family, tuning, chunk, groups):
-    """Template instance and grid.y of one float32 launch of an OSPR pass at H x W (the
-    row-first layout runs its middle pass on lines of length H)."""
+    """Template instance and grid.y of one float32 launch of an OSPR pass at H x W."""
     ci, cf, rv = tuning["col_ifft_variant"], tuning["col_fft_variant"], tuning["row_variant"]
-    if tuning.get("layout", 0) == 1:
-        return {"ospr_row_gen": (f"k_ospr_row_gen<{W}>", chunk),
-                "ospr_row_acc": (f"k_ospr_row_acc<{W}>", groups),
-                "ospr_row": (f"k_ospr_row<{H}, {rv}, 1, 0, 0>", chunk)}.get(family, (None, None))
     return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {ci}, 0>", chunk),
             "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cf}, 0>", groups),
             "ospr_row": (f"k_ospr_row<{W}, {rv}, 1, 0, 0>", chunk)}.get(family, (None, None))
@@ -332,7 +321,7 @@ def run_ours(args):
 
     # FFT tile variants and chunking for this shape, picked by the library's autotuner
     tune_ms = holo.ospr_autotune(H, W, N_SF, reps=5, stream=s) if not args.no_tune else None
-    tuning = dict(holo.ospr_tuning_get(H, W), layout=holo.ospr_tuning_layout_get(H, W))
+    tuning = holo.ospr_tuning_get(H, W)
     ws = torch.empty(holo.ospr_workspace_size(H, W, N_SF), dtype=torch.uint8, device=dev)
     bws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=dev)
 
@@ -367,8 +356,7 @@ def run_ours(args):
     seq_ms = timed_steps(step_sequential, args.steps, profile=True)
     seq_total = max_over_ranks(float(sum(seq_ms)))
     seq_value = world * subframes_per_step * args.steps / (seq_total / 1e3)
-    fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_row_gen", "ospr_row_acc",
-            "ospr_bits_transpose", "ospr_finalize", "replay_error"]
+    fams = ["lut_build", "ospr_col_ifft", "ospr_row", "ospr_col_fft", "ospr_finalize", "replay_error"]
     prof = {f: holo.holo_profile_read(f) for f in fams}
     npairs = (N_SF + 1) // 2
     chunk = min(npairs, tuning["chunk"])
@@ -552,7 +540,7 @@ def run_batch_leg(dev, stream, reps=3):
     tunings = {}
     for (H_, W_) in BATCH_SHAPES:
         holo.ospr_autotune(H_, W_, 24, reps=5, stream=stream.cuda_stream)
-        tunings[f"{H_}x{W_}"] = dict(holo.ospr_tuning_get(H_, W_), layout=holo.ospr_tuning_layout_get(H_, W_))
+        tunings[f"{H_}x{W_}"] = holo.ospr_tuning_get(H_, W_)
     bufs = []
     descs = []
     for k, (H, W, N, L, seed) in enumerate(frames):

@@ -205,26 +205,6 @@ int ospr_tuning_set(int H, int W, int col_ifft_variant, int col_fft_variant, int
                     int groups);
 
 /*
- * OSPR pass layout per shape (H, W), an engineering choice that leaves the method
- * unchanged (the 2D transforms of Eq. 1 and Eq. 2 are separable, so their 1D passes may
- * run in either order):
- *   0  column-first: build + column IDFT; row IDFT + binarise + row DFT; column DFT.
- *   1  row-first: build + row IDFT with the field stored transposed; column IDFT +
- *      binarise + column DFT on the transposed field; row DFT. Every line FFT stays
- *      within the threads of its line (warp-synchronous up to 1024 points), and the
- *      frame's bits are turned to the row-major packing once at the end; the workspace
- *      grows by N*H*W/8 bytes for them. The middle pass uses the row-pass tiles of line
- *      length H (ospr_tuning_set's row_variant); the column variants are unused.
- * Both give the same bits and, up to float32 rounding order, the same replay. The default
- * is 1 (environment override HOLO_OSPR_LAYOUT=0|1); ospr_autotune times both. The
- * tensor-core precisions, Fresnel propagation and ospr_generate_noalloc always run layout
- * 0. ospr_tuning_set keeps the layout; query ospr_workspace_size after a change.
- * Host-only calls; HOLO_EINVAL for a layout other than 0 or 1.
- */
-int ospr_tuning_layout_set(int H, int W, int layout);
-int ospr_tuning_layout_get(int H, int W, int* layout);
-
-/*
  * ospr_generate_noalloc - ospr_generate for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a deployment variant, not part of the method.
  *

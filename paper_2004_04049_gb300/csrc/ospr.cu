@@ -20,10 +20,6 @@
 //   row       rows:    row IDFT, binarise (bits out), row DFT of h_{s0} + i h_{s1}
 //   col_fft   columns: column DFT, S += |Z|^2 over the pairs of a group
 // then finalize: I(k) = (sum_g S_g(k) + S_g(-k)) / (2*N*H*W).
-// The row-first layout (ospr_rowfirst.cu) runs the same transforms in the other order,
-// every line FFT warp-synchronous: build + row IDFT (field stored transposed), column
-// IDFT + binarise + column DFT on the transposed field, row DFT + accumulate; the bits
-// of a frame are transposed to the row-major packing once at the end.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -96,18 +92,14 @@ int fresnel_chirp_build(int H, int W, double kappa, float2* d_chirp, cudaStream_
 // replaces them per shape with the fastest measured candidate, and HOLO_TUNE_CACHE names
 // a file that keeps the choices across processes. The workspace size follows the tuning
 // of the shape.
-// `layout` 0 runs the column-first passes, 1 the row-first passes (whose middle pass is
-// the row pass on lines of length H: row_v then selects its tiles for length H).
 struct OsprTuning {
     int ci_v, cf_v, row_v, chunk, groups;
-    int layout = 0;
 };
 
 static OsprTuning clamp_variants(int H, int W, OsprTuning t) {
-    if (t.layout < 0 || t.layout > 1) t.layout = 0;
     if (t.ci_v < 0 || t.ci_v >= col_variants(H)) t.ci_v = 0;
     if (t.cf_v < 0 || t.cf_v >= col_variants(H)) t.cf_v = 0;
-    if (t.row_v < 0 || t.row_v >= row_variants(t.layout ? H : W)) t.row_v = 0;
+    if (t.row_v < 0 || t.row_v >= row_variants(W)) t.row_v = 0;
     return t;
 }
 
@@ -120,8 +112,7 @@ static int env_int(const char* name, int lo, int hi, int dflt) {
 
 static OsprTuning default_tuning() {
     static const OsprTuning t{0, 0, 0, env_int("HOLO_OSPR_CHUNK", 1, kMaxChunkPairs, kMaxChunkPairs),
-                              env_int("HOLO_OSPR_GROUPS", 1, kMaxGroups, kMaxGroups),
-                              env_int("HOLO_OSPR_LAYOUT", 0, 1, 1)};
+                              env_int("HOLO_OSPR_GROUPS", 1, kMaxGroups, kMaxGroups)};
     return t;
 }
 
@@ -136,12 +127,12 @@ static void tune_cache_load_locked() {
     if (!path || !*path) return;
     FILE* f = fopen(path, "r");
     if (!f) return;
-    int H, W, ci, cf, rv, ch, gr, lay;
+    int H, W, ci, cf, rv, ch, gr;
     while (fscanf(f, " {\"H\": %d, \"W\": %d, \"col_ifft_variant\": %d, \"col_fft_variant\": %d, "
-                     "\"row_variant\": %d, \"chunk\": %d, \"groups\": %d, \"layout\": %d}",
-                  &H, &W, &ci, &cf, &rv, &ch, &gr, &lay) == 8) {
+                     "\"row_variant\": %d, \"chunk\": %d, \"groups\": %d}",
+                  &H, &W, &ci, &cf, &rv, &ch, &gr) == 7) {
         if (ch < 1 || ch > kMaxChunkPairs || gr < 1 || gr > kMaxGroups) continue;
-        g_tune[{H, W}] = clamp_variants(H, W, OsprTuning{ci, cf, rv, ch, gr, lay});
+        g_tune[{H, W}] = clamp_variants(H, W, OsprTuning{ci, cf, rv, ch, gr});
     }
     fclose(f);
 }
@@ -153,9 +144,8 @@ static void tune_cache_save_locked() {
     if (!f) return;
     for (const auto& kv : g_tune)
         fprintf(f, "{\"H\": %d, \"W\": %d, \"col_ifft_variant\": %d, \"col_fft_variant\": %d, "
-                   "\"row_variant\": %d, \"chunk\": %d, \"groups\": %d, \"layout\": %d}\n", kv.first.first,
-                kv.first.second, kv.second.ci_v, kv.second.cf_v, kv.second.row_v, kv.second.chunk, kv.second.groups,
-                kv.second.layout);
+                   "\"row_variant\": %d, \"chunk\": %d, \"groups\": %d}\n", kv.first.first, kv.first.second,
+                kv.second.ci_v, kv.second.cf_v, kv.second.row_v, kv.second.chunk, kv.second.groups);
     fclose(f);
 }
 
@@ -173,13 +163,10 @@ static void tuning_install(int H, int W, const OsprTuning& t, bool save) {
     if (save) tune_cache_save_locked();
 }
 
-// Workspace: the chunk's complex fields, the group accumulators and, for the row-first
-// layout, the column-oriented bit words of all N sub-frames (transposed at the end).
 struct OsprPlan {
     int npairs, chunk, groups, ci_v, cf_v, row_v;
     int prec = HOLO_FP32;
-    int layout = 0;
-    size_t z_bytes, s_bytes, t_bytes = 0, total;
+    size_t z_bytes, s_bytes, total;
 };
 
 static OsprPlan ospr_plan_with(int H, int W, int N, const OsprTuning& t) {
@@ -192,11 +179,9 @@ static OsprPlan ospr_plan_with(int H, int W, int N, const OsprTuning& t) {
     pl.ci_v = c.ci_v;
     pl.cf_v = c.cf_v;
     pl.row_v = c.row_v;
-    pl.layout = c.layout;
     pl.z_bytes = align_up(size_t(pl.chunk) * P * sizeof(float2), 256);
     pl.s_bytes = align_up(size_t(pl.groups) * P * sizeof(float), 256);
-    pl.t_bytes = pl.layout ? align_up(size_t(N) * (P / 8), 256) : 0;
-    pl.total = pl.z_bytes + pl.s_bytes + pl.t_bytes;
+    pl.total = pl.z_bytes + pl.s_bytes;
     return pl;
 }
 
@@ -208,7 +193,6 @@ static OsprPlan ospr_plan(int H, int W, int N, int precision = HOLO_FP32) {
     if (precision != HOLO_FP32) {
         t.ci_v = t.cf_v = kTcColVariant;
         t.row_v = kTcRowVariant;
-        t.layout = 0;
     }
     OsprPlan pl = ospr_plan_with(H, W, N, t);
     pl.prec = precision;
@@ -239,33 +223,9 @@ static int check_shape(const char* who, int H, int W) {
 }
 
 // chunks of sub-frame pairs through the three passes, then the symmetrising finalize
-// row-first layout: the passes of every chunk, then the bits of all sub-frames turned to
-// the row-major packing (bits_t: N*H*W/8 bytes of workspace)
-static int ospr_run_rowfirst(OsprArgs& a, const OsprPlan& pl, bool replay, uint32_t* bits_t, cudaStream_t st) {
+static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_replay, cudaStream_t st) {
     int rc;
-    uint32_t* bits = a.bits;
-    OsprArgs at = a;          // the middle pass sees the transposed field: W lines of length H
-    at.H = a.W;
-    at.W = a.H;
-    at.bits = bits ? bits_t : nullptr;
     for (int first = 0; first < pl.npairs; first += pl.chunk) {
-        a.first_pair = at.first_pair = first;
-        a.pairs = at.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
-        a.accumulate = at.accumulate = first > 0;
-        if ((rc = ospr_run_row_gen(a, st))) return rc;
-        if ((rc = ospr_run_row(at, pl.row_v, replay, st))) return rc;
-        if (replay && (rc = ospr_run_row_acc(a, st))) return rc;
-    }
-    if (bits && (rc = ospr_run_bits_transpose(bits_t, bits, a.H, a.W, a.N, st))) return rc;
-    return HOLO_OK;
-}
-
-static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_replay, cudaStream_t st,
-                    uint32_t* bits_t = nullptr) {
-    int rc;
-    if (pl.layout == 1 && pl.prec == HOLO_FP32 && !a.fresnel) {
-        if ((rc = ospr_run_rowfirst(a, pl, replay, bits_t, st))) return rc;
-    } else for (int first = 0; first < pl.npairs; first += pl.chunk) {
         a.first_pair = first;
         a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
         a.accumulate = first > 0;
@@ -375,9 +335,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.tc05b = tab.tc05b[precision];
     a.fresnel = 0;
     a.chirp_y = a.chirp_x = nullptr;
-    uint32_t* bits_t = pl.layout ? reinterpret_cast<uint32_t*>(static_cast<char*>(d_ws) + pl.z_bytes + pl.s_bytes)
-                                 : nullptr;
-    if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s), bits_t))) return rc;
+    if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
     ospr_design_rules(L, N, H, W);
     return HOLO_OK;
 }
@@ -385,12 +343,7 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
 // Fresnel propagation: one sub-frame per field slot, so the plan of 2N sub-frames gives N
 // slots; the chirp tables (H + W complex64) follow the plan's buffers.
 static OsprPlan fresnel_plan(int H, int W, int N, size_t* chirp_off) {
-    OsprTuning t = tuning_for(H, W);
-    if (t.layout) {   // Fresnel frames run the column-first passes: keep that layout's tiles
-        t = default_tuning();
-        t.layout = 0;
-    }
-    OsprPlan pl = ospr_plan_with(H, W, 2 * N, t);
+    OsprPlan pl = ospr_plan(H, W, 2 * N, HOLO_FP32);
     *chirp_off = pl.total;
     pl.total += align_up(size_t(H + W) * sizeof(float2), 256);
     return pl;
@@ -483,29 +436,8 @@ extern "C" int ospr_tuning_set(int H, int W, int col_ifft_variant, int col_fft_v
         groups > kMaxGroups)
         return fail(HOLO_EINVAL, "ospr_tuning_set: column variants 0..2, row variant 0..1, chunk 1..%d, groups 1..%d",
                     kMaxChunkPairs, kMaxGroups);
-    const int layout = tuning_for(H, W).layout;   // kept: ospr_tuning_layout_set chooses it
     tuning_install(H, W, clamp_variants(H, W, OsprTuning{col_ifft_variant, col_fft_variant, row_variant, chunk,
-                                                         groups, layout}), false);
-    return HOLO_OK;
-}
-
-extern "C" int ospr_tuning_layout_set(int H, int W, int layout) {
-    clear_error();
-    int rc = check_shape("ospr_tuning_layout_set", H, W);
-    if (rc) return rc;
-    if (layout < 0 || layout > 1) return fail(HOLO_EINVAL, "ospr_tuning_layout_set: layout %d is not 0 or 1", layout);
-    OsprTuning t = tuning_for(H, W);
-    t.layout = layout;
-    tuning_install(H, W, clamp_variants(H, W, t), false);
-    return HOLO_OK;
-}
-
-extern "C" int ospr_tuning_layout_get(int H, int W, int* layout) {
-    clear_error();
-    int rc = check_shape("ospr_tuning_layout_get", H, W);
-    if (rc) return rc;
-    if (!layout) return fail(HOLO_EINVAL, "ospr_tuning_layout_get: NULL output");
-    *layout = clamp_variants(H, W, tuning_for(H, W)).layout;
+                                                         groups}), false);
     return HOLO_OK;
 }
 
@@ -519,7 +451,7 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
     const size_t P = size_t(H) * W;
     const int64_t L = 10007;
     // the largest candidate plan bounds the workspace
-    const size_t ws_bytes = ospr_plan_with(H, W, N, OsprTuning{0, 0, 0, kMaxChunkPairs, kMaxGroups, 1}).total;
+    const size_t ws_bytes = ospr_plan_with(H, W, N, OsprTuning{0, 0, 0, kMaxChunkPairs, kMaxGroups}).total;
     if (fault_injected("alloc")) return fail(HOLO_ENOMEM, "%s: injected allocation failure (HOLO_FAULT_INJECT)", who);
     void *d_t = nullptr, *d_codes = nullptr, *d_bits = nullptr, *d_rep = nullptr, *d_ws = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -567,7 +499,7 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
         *ms = v[reps / 2];
         return HOLO_OK;
     };
-    OsprTuning best{0, 0, 0, kMaxChunkPairs < npairs ? kMaxChunkPairs : npairs, kMaxGroups, default_tuning().layout};
+    OsprTuning best{0, 0, 0, kMaxChunkPairs < npairs ? kMaxChunkPairs : npairs, kMaxGroups};
     float best_t = 0.f;
     if (!rc) rc = measure(best, &best_t);
     // coordinate descent, two sweeps: column IDFT tiles, row tiles, column DFT tiles,
@@ -588,20 +520,14 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
     const int groups[] = {1, 2, 4};
     for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
         OsprTuning b = best;
-        { OsprTuning t = b; t.layout = 1 - b.layout; t.row_v = 0; consider(t); }
+        for (int v = 0; v < col_variants(H); ++v)
+            if (v != b.ci_v) { OsprTuning t = b; t.ci_v = v; consider(t); }
         b = best;
-        if (b.layout == 0) {   // the column passes' tiles exist in the column-first layout only
-            for (int v = 0; v < col_variants(H); ++v)
-                if (v != b.ci_v) { OsprTuning t = b; t.ci_v = v; consider(t); }
-        }
-        b = best;
-        for (int v = 0; v < row_variants(b.layout ? H : W); ++v)
+        for (int v = 0; v < row_variants(W); ++v)
             if (v != b.row_v) { OsprTuning t = b; t.row_v = v; consider(t); }
         b = best;
-        if (b.layout == 0) {
-            for (int v = 0; v < col_variants(H); ++v)
-                if (v != b.cf_v) { OsprTuning t = b; t.cf_v = v; consider(t); }
-        }
+        for (int v = 0; v < col_variants(H); ++v)
+            if (v != b.cf_v) { OsprTuning t = b; t.cf_v = v; consider(t); }
         b = best;
         for (int c : chunks)
             if (c <= npairs && c != b.chunk) { OsprTuning t = b; t.chunk = c; consider(t); }

@@ -435,12 +435,6 @@ k_ospr_col_fft(OsprArgs a) {
 int ospr_run_col_ifft(const OsprArgs& a, int v, cudaStream_t st);
 int ospr_run_col_fft(const OsprArgs& a, int v, cudaStream_t st);
 int ospr_run_row(const OsprArgs& a, int v, bool replay, cudaStream_t st);
-// row-first layout (ospr_rowfirst.cu): build + row IDFT with a transposed store; the
-// row DFT + accumulate pass reading the transposed field; the bit transposition of a
-// frame's N sub-frames
-int ospr_run_row_gen(const OsprArgs& a, cudaStream_t st);
-int ospr_run_row_acc(const OsprArgs& a, cudaStream_t st);
-int ospr_run_bits_transpose(const uint32_t* bits_t, uint32_t* bits, int H, int W, int N, cudaStream_t st);
 // tensor-core precisions (ospr_tc.cu): lengths 1024 and 2048, fixed tile variants
 int ospr_run_col_ifft_tc(const OsprArgs& a, int prec, cudaStream_t st);
 int ospr_run_col_fft_tc(const OsprArgs& a, int prec, cudaStream_t st);

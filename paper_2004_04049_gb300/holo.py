@@ -108,8 +108,6 @@ _SIGS = {
     "ospr_autotune": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.POINTER(_c.c_double)]),
     "ospr_tuning_get": (_c.c_int, [_c.c_int, _c.c_int] + [_c.POINTER(_c.c_int)] * 5),
     "ospr_tuning_set": (_c.c_int, [_c.c_int] * 7),
-    "ospr_tuning_layout_set": (_c.c_int, [_c.c_int] * 3),
-    "ospr_tuning_layout_get": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_int)]),
     "gs_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "gs_tuning_set": (_c.c_int, [_c.c_int] * 4),
     "gs_tuning_get": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
@@ -356,16 +354,6 @@ def ospr_tuning_get(H, W):
 
 def ospr_tuning_set(H, W, col_ifft_variant=0, col_fft_variant=0, row_variant=0, chunk=16, groups=4):
     return _call("ospr_tuning_set", H, W, col_ifft_variant, col_fft_variant, row_variant, chunk, groups)
-
-
-def ospr_tuning_layout_set(H, W, layout):
-    return _call("ospr_tuning_layout_set", H, W, layout)
-
-
-def ospr_tuning_layout_get(H, W):
-    v = ctypes.c_int(0)
-    _call("ospr_tuning_layout_get", H, W, ctypes.byref(v))
-    return v.value
 
 
 def gs_tuning_set(H, W, col_variant=-1, row_variant=-1):

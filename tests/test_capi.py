@@ -95,40 +95,24 @@ def test_batch_workspace_is_host_only(lib):
 
 
 def test_tuning_set_get_host_only(lib):
-    assert holo.ospr_tuning_layout_get(1024, 1024) == 1          # row-first by default
-    # column-first layout: 256-point columns have one tile variant, so column variants fall
-    # back to 0; 512-point rows keep variant 1
-    holo.ospr_tuning_layout_set(256, 512, 0)
+    # 256-point columns have one tile variant: column variants fall back to 0; 512-point
+    # rows keep variant 1
     holo.ospr_tuning_set(256, 512, 2, 1, 1, 5, 3)
     try:
         t = holo.ospr_tuning_get(256, 512)
         assert t == {"col_ifft_variant": 0, "col_fft_variant": 0, "row_variant": 1, "chunk": 5, "groups": 3}
-        assert holo.ospr_tuning_layout_get(256, 512) == 0           # ospr_tuning_set keeps the layout
-        # row-first: the middle pass runs lines of length H = 256, which have one variant
-        holo.ospr_tuning_layout_set(256, 512, 1)
-        assert holo.ospr_tuning_get(256, 512)["row_variant"] == 0
-        holo.ospr_tuning_layout_set(1024, 1024, 0)
         holo.ospr_tuning_set(1024, 1024, 2, 1, 0, 12, 2)
         t = holo.ospr_tuning_get(1024, 1024)
         assert (t["col_ifft_variant"], t["col_fft_variant"], t["chunk"], t["groups"]) == (2, 1, 12, 2)
-        # the workspace follows the setting: 12 complex64 fields and 2 float32 accumulators,
-        # and for the row-first layout the N*H*W/8 bytes of column-oriented bits
+        # the workspace follows the setting: 12 complex64 fields and 2 float32 accumulators
         assert holo.ospr_workspace_size(1024, 1024, 24) == 12 * 8 * 2**20 + 2 * 4 * 2**20
-        holo.ospr_tuning_layout_set(1024, 1024, 1)
-        assert holo.ospr_workspace_size(1024, 1024, 24) == 12 * 8 * 2**20 + 2 * 4 * 2**20 + 24 * 2**17
         for bad in [(3, 0, 0, 4, 1), (0, -1, 0, 4, 1), (0, 0, 2, 4, 1), (0, 0, 0, 17, 1), (0, 0, 0, 4, 5)]:
             with pytest.raises(holo.HoloError) as ei:
                 holo.ospr_tuning_set(1024, 1024, *bad)
             assert ei.value.status == holo.HOLO_EINVAL
-        for bad in (-1, 2):
-            with pytest.raises(holo.HoloError) as ei:
-                holo.ospr_tuning_layout_set(1024, 1024, bad)
-            assert ei.value.status == holo.HOLO_EINVAL
     finally:
         holo.ospr_tuning_set(256, 512)
         holo.ospr_tuning_set(1024, 1024)
-        holo.ospr_tuning_layout_set(256, 512, 1)
-        holo.ospr_tuning_layout_set(1024, 1024, 1)
 
 
 def test_gs_tuning_host_only(lib):

@@ -20,26 +20,14 @@ from synthetic import blob_target, noise_target
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_ospr(cuda, T, N, L, seed, levels=256, start=0, stride=0, layout=None):
-    """One ospr_generate call; `layout` (0 column-first, 1 row-first) is set for the shape
-    for this call only (None keeps the default)."""
-    H, W = T.shape
-    before = holo.ospr_tuning_layout_get(H, W)
-    if layout is not None:
-        holo.ospr_tuning_layout_set(H, W, layout)
-    try:
-        t = torch.from_numpy(T).to(cuda)
-        codes = pipeline.lut(seed, L, levels, device=cuda) if L > 0 else None
-        bits, I = pipeline.ospr(t, N, codes, L, levels, seed, start, stride)
-        err = pipeline.error(I, t)
-        torch.cuda.synchronize()
-    finally:
-        holo.ospr_tuning_layout_set(H, W, before)
+def _gpu_ospr(cuda, T, N, L, seed, levels=256, start=0, stride=0):
+    t = torch.from_numpy(T).to(cuda)
+    codes = pipeline.lut(seed, L, levels, device=cuda) if L > 0 else None
+    bits, I = pipeline.ospr(t, N, codes, L, levels, seed, start, stride)
+    err = pipeline.error(I, t)
+    torch.cuda.synchronize()
     return (bits.cpu().numpy().view(np.uint32), I.cpu().numpy(), err.cpu().numpy(),
             codes.cpu().numpy().astype(np.int64) if codes is not None else None)
-
-
-LAYOUTS = [0, 1]   # column-first and row-first passes: both must meet the same bounds
 
 
 CASES = [
@@ -58,12 +46,11 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("H,W,N,L,kind", CASES)
-def test_parity_elementwise(cuda, H, W, N, L, kind, layout):
+def test_parity_elementwise(cuda, H, W, N, L, kind):
     T = blob_target(H, W, 1000) if kind == "blob" else noise_target(H, W, 2000)
     seed = 7
-    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, N, L, seed, layout=layout)
+    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, N, L, seed)
     table = olut.lut_codes(seed, L) if L > 0 else None
     if L > 0:
         assert np.array_equal(gcodes, table)
@@ -83,12 +70,11 @@ def test_parity_elementwise(cuda, H, W, N, L, kind, layout):
         check_nmse(gerr[2], o_e2e[2])
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("levels", [2, 16])
-def test_parity_other_code_levels(cuda, levels, layout):
+def test_parity_other_code_levels(cuda, levels):
     H = W = 128
     T = blob_target(H, W, 1001)
-    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, 4, 1031, 9, levels=levels, layout=layout)
+    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, 4, 1031, 9, levels=levels)
     table = olut.lut_codes(9, 1031, levels)
     assert np.array_equal(gcodes, table)
     ob, oI, ex = oospr.ospr(T, 4, table, 1031, 9, levels=levels, keep_fields=True)
@@ -96,11 +82,10 @@ def test_parity_other_code_levels(cuda, levels, layout):
     check_replay(gI, oospr.replay_from_bits(gb, H, W))
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
-def test_start_and_stride(cuda, layout):
+def test_start_and_stride(cuda):
     H, W, N, L = 64, 64, 4, 997
     T = blob_target(H, W, 1002)
-    gb, gI, _, _ = _gpu_ospr(cuda, T, N, L, 3, start=12345, stride=777, layout=layout)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, L, 3, start=12345, stride=777)
     table = olut.lut_codes(3, L)
     ob, oI, ex = oospr.ospr(T, N, table, L, 3, start=12345, stride=777, keep_fields=True)
     check_bits(gb, ob, ex["re_h"], H * W)
@@ -117,11 +102,10 @@ def test_continuation_between_frames(cuda):
     assert np.array_equal(a[3:], b)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
-def test_invariants_on_gpu_outputs(cuda, layout):
+def test_invariants_on_gpu_outputs(cuda):
     H, W, N = 256, 512, 6
     T = noise_target(H, W, 2001)
-    gb, gI, _, _ = _gpu_ospr(cuda, T, N, 10007, 1, layout=layout)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, 10007, 1)
     twin = np.roll(np.flip(gI), shift=(1, 1), axis=(0, 1))
     assert np.array_equal(gI, twin)                    # symmetrised by construction
     assert abs(gI.sum() / (H * W) - 1.0) < 1e-4        # unitarity: energy P per sub-frame
@@ -136,13 +120,12 @@ def test_length_dividing_pixels_repeats_subframes(cuda):
         assert np.mean(bits[s] == bits[0]) >= 0.9999
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
-def test_long_table_equals_generator_bit_exact(cuda, layout):
+def test_long_table_equals_generator_bit_exact(cuda):
     H = W = 64
     N = 3
     T = blob_target(H, W, 1005)
-    a, Ia, _, _ = _gpu_ospr(cuda, T, N, N * H * W, 11, layout=layout)
-    b, Ib, _, _ = _gpu_ospr(cuda, T, N, holo.L_UNREPEATED, 11, layout=layout)
+    a, Ia, _, _ = _gpu_ospr(cuda, T, N, N * H * W, 11)
+    b, Ib, _, _ = _gpu_ospr(cuda, T, N, holo.L_UNREPEATED, 11)
     assert np.array_equal(a, b)
     assert np.array_equal(Ia, Ib)
 
@@ -169,28 +152,26 @@ def test_deterministic(cuda):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
-def test_many_pairs_span_chunks(cuda, layout):
-    # more pairs than one chunk holds: the accumulator carries across chunks
+def test_many_pairs_span_chunks(cuda):
+    # more pairs than one chunk holds: the column accumulator carries across chunks
     H = W = 64
     N = 37
     T = blob_target(H, W, 1008)
-    gb, gI, _, _ = _gpu_ospr(cuda, T, N, 10007, 6, layout=layout)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, 10007, 6)
     table = olut.lut_codes(6, 10007)
     ob, oI, ex = oospr.ospr(T, N, table, 10007, 6, keep_fields=True)
     check_bits(gb, ob, ex["re_h"], H * W)
     check_replay(gI, oospr.replay_from_bits(gb, H, W))
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
-def test_full_size_1024_sampled(cuda, layout):
+def test_full_size_1024_sampled(cuda):
     """The benchmark workload (1024x1024, N = 24) in its launch configuration: sub-frames
     0 and 23 element by element, the replay at sampled pixels by direct DFT sums of the
     GPU's bits, the NMSE from the GPU replay."""
     H = W = 1024
     N, L, seed = 24, 10007, 7
     T = blob_target(H, W, 1000)
-    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, N, L, seed, layout=layout)
+    gb, gI, gerr, gcodes = _gpu_ospr(cuda, T, N, L, seed)
     table = olut.lut_codes(seed, L)
     assert np.array_equal(gcodes, table)
     P = H * W
@@ -213,8 +194,7 @@ def test_full_size_1024_sampled(cuda, layout):
     check_nmse(gerr[2], o_stage[2])
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
-def test_largest_size_4096(cuda, layout):
+def test_largest_size_4096(cuda):
     """The largest supported shape (4096x4096, N = 2): sub-frame 0 element by element, the
     replay's symmetry and unitarity, and sampled replay pixels by direct DFT sums of the
     GPU's bits."""
@@ -222,7 +202,7 @@ def test_largest_size_4096(cuda, layout):
     N, L, seed = 2, 10007, 3
     P = H * W
     T = blob_target(H, W, 1010)
-    gb, gI, _, _ = _gpu_ospr(cuda, T, N, L, seed, layout=layout)
+    gb, gI, _, _ = _gpu_ospr(cuda, T, N, L, seed)
     table = olut.lut_codes(seed, L)
     c = olut.subframe_codes(table, L, seed, 0, 0, P, P)
     Hs = oospr.back_propagate(oospr.subframe_field(T, c))
@@ -237,17 +217,3 @@ def test_largest_size_4096(cuda, layout):
         ph = np.exp(-2j * np.pi * (u * r / H + v * cc / W))
         R = np.tensordot(hs, ph, axes=([1, 2], [0, 1])) / np.sqrt(P)
         assert abs(gI[u, v] - np.mean(np.abs(R) ** 2)) <= 1e-4 * gI.max()
-
-
-def test_layouts_agree_on_mixed_shapes(cuda):
-    # the two pass orders compute the same transforms: bits agree on every pixel whose
-    # |Re H| is decidable and the replays agree to float32 rounding, for square and
-    # non-square shapes whose row and column lengths take different tile configurations
-    for (H, W, N, L) in [(512, 2048, 4, 4099), (2048, 512, 3, 10007), (1024, 1024, 24, 2 ** 20)]:
-        T = blob_target(H, W, 1011)
-        a, Ia, _, _ = _gpu_ospr(cuda, T, N, L, 8, layout=0)
-        b, Ib, _, _ = _gpu_ospr(cuda, T, N, L, 8, layout=1)
-        diff = unpack(a, H * W) != unpack(b, H * W)
-        assert diff.mean() <= 1e-4, (H, W, diff.mean())
-        if not diff.any():
-            assert np.abs(Ia - Ib).max() <= 1e-5 * Ia.max(), (H, W)

@@ -31,15 +31,11 @@ def _oracle(T, H, W, N, L, seed):
     return _ORACLE[key]
 
 
-@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("H,W,N", [(512, 512, 7), (1024, 1024, 4), (2048, 512, 3), (512, 2048, 3)])
 @pytest.mark.parametrize("setting", SETTINGS)
-def test_setting_parity(cuda, H, W, N, setting, layout):
-    # layout 0 runs every column and row tile variant; layout 1 runs the middle pass's row
-    # variants on lines of length H (the column variants are unused there)
+def test_setting_parity(cuda, H, W, N, setting):
     L, seed = 10007, 5
     T = blob_target(H, W, 1200)
-    holo.ospr_tuning_layout_set(H, W, layout)
     holo.ospr_tuning_set(H, W, *setting)
     try:
         t = torch.from_numpy(T).to(cuda)
@@ -50,7 +46,6 @@ def test_setting_parity(cuda, H, W, N, setting, layout):
         gI = I.cpu().numpy()
     finally:
         holo.ospr_tuning_set(H, W)
-        holo.ospr_tuning_layout_set(H, W, 1)
     ob, re_h = _oracle(T, H, W, N, L, seed)
     check_bits(gb, ob, re_h, H * W)
     check_replay(gI, oospr.replay_from_bits(gb, H, W))
@@ -91,7 +86,6 @@ def test_autotune_installs_and_records(cuda, tmp_path):
     rec = [r for r in rows if r["H"] == 512 and r["W"] == 1024]
     assert rec and rec[0]["chunk"] == t["chunk"] and rec[0]["col_ifft_variant"] == t["col_ifft_variant"]
     assert rec[0]["col_fft_variant"] == t["col_fft_variant"] and rec[0]["row_variant"] == t["row_variant"]
-    assert rec[0]["layout"] == holo.ospr_tuning_layout_get(512, 1024) in (0, 1)
     # the tuned setting still computes the same bits as the default one, up to ties
     T = blob_target(512, 1024, 1201)
     tt = torch.from_numpy(T).to(cuda)
