@@ -418,6 +418,28 @@ int gs_iterate_fresnel(const float* d_target, int H, int W, int iters, int level
                        void* d_ws, size_t ws_bytes, holo_stream_t s);
 
 /*
+ * gs_iterate_batch - gs_iterate for B targets of one shape in the same launches (every
+ * pass covers all targets, so small fields fill the GPU together). Target b is
+ * d_targets + b*H*W and every per-target input and output advances the same way:
+ *   d_targets      [B][H][W] float32.
+ *   d_init_phases  [B][H][W] float32 radians or NULL.
+ *   d_states_in    [B][H][W][2] float32 or NULL.
+ *   d_phase_codes  [B][H][W] uint8 or NULL; d_replay [B][H][W] float32 or NULL;
+ *   d_err          [B][iters] float64 or NULL; d_states_out [B][H][W][2] or NULL.
+ * With the LUT start, target b draws its initial phases at start_index + b*H*W + p: the
+ * targets continue the table like consecutive frames (Fig. 3; Section 8's rule for GS
+ * video: every frame gets fresh phases). Each target's results equal those of gs_iterate
+ * with start_index + b*H*W. 1 <= B <= 65535 and B*H*W <= 2^31; other arguments and
+ * errors as gs_iterate. gs_batch_workspace_size gives the workspace of B targets.
+ */
+int gs_batch_workspace_size(int B, int H, int W, int iters, int precision, size_t* bytes);
+int gs_iterate_batch(const float* d_targets, int B, int H, int W, int iters, int levels,
+                     const float* d_init_phases, const uint8_t* d_codes, int64_t L, int lut_levels,
+                     uint64_t seed, int64_t start_index, int precision, uint8_t* d_phase_codes,
+                     float* d_replay, double* d_err, const float* d_states_in, float* d_states_out,
+                     void* d_ws, size_t ws_bytes, holo_stream_t s);
+
+/*
  * gs_state_phase - the replay-plane phase of a GS state (Section 2: GS keeps the phase of
  * the replay field and resets its amplitude to the target): d_phase[p] = arg(E_p) in
  * (-pi, pi] with arg(0) = 0, E = d_state (the [H][W][2] float32 (re, im) field that

@@ -13,6 +13,8 @@
 //              (the next iteration's first half); on the last iteration it writes
 //              |R|^2 and the state instead of transforming back
 //   finish     per-iteration error sums (float-float, converted to float64 once)
+// A batch of B targets of one shape runs through the same launches: blockIdx.y is the
+// target, every buffer holds B fields of H*W (gs_iterate is the batch of one).
 #include <cmath>
 #include <cstdlib>
 #include <map>
@@ -76,8 +78,9 @@ struct GsArgs {
     float2* y;                   // [H][W] complex work field
     GsScalars* sc;
     const ff* prep_part;         // [kGsPrepBlocks] partial sums of T^2
-    ff* err_part;                // [iters][col blocks] partial error sums
-    int iter;
+    ff* err_part;                // [targets][iters][col blocks] partial error sums
+    int iter, iters;
+    int batch;                   // targets (grid.y of every launch)
     uint8_t* codes_out;
     float* replay_out;
     float2* state_out;
@@ -102,11 +105,31 @@ constexpr size_t gs_row_smem() {
     return sizeof(float2) * (kCsSmemEntries + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
 }
 
+// The arguments of target b of a batch: every per-target buffer advances by b fields;
+// the initial phases continue the table draw (target b = sub-frame b of the draw rule)
+__device__ __forceinline__ GsArgs gs_target(const GsArgs& a0, int b) {
+    GsArgs a = a0;
+    const size_t P = size_t(a.H) * a.W;
+    const size_t off = size_t(b) * P;
+    a.target += off;
+    if (a.init_phase) a.init_phase += off;
+    if (a.state_in) a.state_in += off;
+    a.y += off;
+    a.sc += b;
+    a.prep_part += size_t(b) * kGsPrepBlocks;
+    if (a.codes_out) a.codes_out += off;
+    if (a.replay_out) a.replay_out += off;
+    if (a.state_out) a.state_out += off;
+    return a;
+}
+
 // ----------------------------------------------------------------- prepare ----
 // per-block float-float partials of sum T^2
 __global__ void __launch_bounds__(kGsPrepThreads)
 k_gs_prepare(const float* __restrict__ T, int64_t P, ff* __restrict__ partials) {
     __shared__ ff sm[32];
+    T += int64_t(blockIdx.y) * P;                  // target blockIdx.y of the batch
+    partials += size_t(blockIdx.y) * kGsPrepBlocks;
     float acc[1] = {0.f};
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P; i += int64_t(gridDim.x) * blockDim.x)
         acc[0] = fmaf(T[i], T[i], acc[0]);
@@ -124,8 +147,9 @@ __device__ __forceinline__ float gs_scale(const ff* __restrict__ partials, int64
 // --------------------------------------------------------------- col_init ----
 template <int NC, int V>
 __global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC)
-k_gs_col_init(GsArgs a) {
+k_gs_col_init(GsArgs a0) {
     constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
+    const GsArgs a = gs_target(a0, blockIdx.y);
     extern __shared__ float2 sm[];
     float2* cs = sm;
     float2* lines = sm + 256;
@@ -145,7 +169,7 @@ k_gs_col_init(GsArgs a) {
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
     const float scale = s_scale;
-    const SubframeDraw d0 = subframe_draw(a.ps, 0);
+    const SubframeDraw d0 = subframe_draw(a.ps, blockIdx.y);
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) {
@@ -170,8 +194,9 @@ k_gs_col_init(GsArgs a) {
 // FRESNEL: the hologram field is conj(Q) * IDFT(E) and the replay transform takes h * Q.
 template <int NR, int V, bool FRESNEL = false>
 __global__ void __launch_bounds__((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR)
-k_gs_row(GsArgs a) {
+k_gs_row(GsArgs a0) {
     constexpr int R = GsRowCfg<NR, V>::R, T = NR / R;
+    const GsArgs a = gs_target(a0, blockIdx.y);
     constexpr bool BLOCK = T > 32;
     extern __shared__ float2 sm[];
     float2* cs = sm;
@@ -215,8 +240,9 @@ k_gs_row(GsArgs a) {
 template <int NC, int V, bool LAST>
 __global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC,
                                   (NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC <= 256 ? 2 : 1)
-k_gs_col(GsArgs a) {
+k_gs_col(GsArgs a0) {
     constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
+    const GsArgs a = gs_target(a0, blockIdx.y);
     extern __shared__ float2 sm[];
     __shared__ ff red[32];
     float2* lines = sm;
@@ -260,7 +286,8 @@ k_gs_col(GsArgs a) {
     const float errv[1] = {err};
     ff b[1];
     block_sums_ff<1>(errv, b, red);
-    if (threadIdx.x == 0) a.err_part[size_t(a.iter) * gridDim.x + blockIdx.x] = b[0];
+    if (threadIdx.x == 0)
+        a.err_part[(size_t(blockIdx.y) * a.iters + size_t(a.iter)) * gridDim.x + blockIdx.x] = b[0];
     if constexpr (!LAST) {
         line_fft<NC, R, +1, true>(v, buf, t, a.tw);
         pdl_trigger();
@@ -273,8 +300,9 @@ k_gs_col(GsArgs a) {
 __global__ void __launch_bounds__(32)
 k_gs_finish(const ff* __restrict__ err_part, int nb, double* __restrict__ err) {
     pdl_wait();
-    const ff v = warp_sum_array_ff(err_part + size_t(blockIdx.x) * nb, nb);
-    if (threadIdx.x == 0) err[blockIdx.x] = ff_to_double(v);
+    const size_t k = size_t(blockIdx.y) * gridDim.x + blockIdx.x;   // target blockIdx.y, iteration blockIdx.x
+    const ff v = warp_sum_array_ff(err_part + k * nb, nb);
+    if (threadIdx.x == 0) err[k] = ff_to_double(v);
 }
 
 // ------------------------------------------------------------------- host ----
@@ -307,8 +335,8 @@ static int launch_col_init(const GsArgs& a, cudaStream_t st) {
     int rc = ensure_smem((const void*)k_gs_col_init<NC, V>, smem, &mask);
     if (rc) return rc;
     Launch ln("gs_col_init", st);
-    const cudaError_t le = launch_pdl(k_gs_col_init<NC, V>, dim3(a.W / GsColCfg<NC, V>::LPC), dim3((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC),
-               smem, st, a);
+    const cudaError_t le = launch_pdl(k_gs_col_init<NC, V>, dim3(a.W / GsColCfg<NC, V>::LPC, a.batch),
+                                      dim3((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC), smem, st, a);
     return ln.done("gs_col_init launch", le);
 }
 template <int NR, int V, bool FRESNEL>
@@ -318,7 +346,7 @@ static int launch_row_kind(const GsArgs& a, cudaStream_t st) {
     int rc = ensure_smem((const void*)k_gs_row<NR, V, FRESNEL>, smem, &mask);
     if (rc) return rc;
     Launch ln("gs_row", st);
-    const cudaError_t le = launch_pdl(k_gs_row<NR, V, FRESNEL>, dim3(a.H / GsRowCfg<NR, V>::LPR),
+    const cudaError_t le = launch_pdl(k_gs_row<NR, V, FRESNEL>, dim3(a.H / GsRowCfg<NR, V>::LPR, a.batch),
                                       dim3((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR), smem, st, a);
     return ln.done("gs_row launch", le);
 }
@@ -330,7 +358,7 @@ template <int NC, int V>
 static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
     static uint64_t mask0 = 0, mask1 = 0;
     constexpr size_t smem = sizeof(float2) * size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>();
-    const dim3 grid(a.W / GsColCfg<NC, V>::LPC), threads((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC);
+    const dim3 grid(a.W / GsColCfg<NC, V>::LPC, a.batch), threads((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC);
     int rc = last ? ensure_smem((const void*)k_gs_col<NC, V, true>, smem, &mask1)
                   : ensure_smem((const void*)k_gs_col<NC, V, false>, smem, &mask0);
     if (rc) return rc;
@@ -377,15 +405,16 @@ static int col_blocks(int H, int W, int cv) {
 struct GsLayout {
     size_t y_off, sc_off, prep_off, err_off, chirp_off, total;
 };
-static GsLayout gs_layout(int H, int W, int iters) {
+// B targets: B complex fields, scalars, T^2 partials and error partials, then the chirp
+static GsLayout gs_layout(int H, int W, int iters, int B = 1) {
     GsLayout l;
     const size_t P = size_t(H) * W;
     l.y_off = 0;
-    l.sc_off = align_up(P * sizeof(float2), 256);
-    l.prep_off = l.sc_off + align_up(sizeof(GsScalars), 256);
-    l.err_off = l.prep_off + align_up(sizeof(ff) * kGsPrepBlocks, 256);
+    l.sc_off = align_up(size_t(B) * P * sizeof(float2), 256);
+    l.prep_off = l.sc_off + align_up(size_t(B) * sizeof(GsScalars), 256);
+    l.err_off = l.prep_off + align_up(sizeof(ff) * kGsPrepBlocks * size_t(B), 256);
     // error partials for the column tiles with the fewest lines (any variant fits)
-    l.chirp_off = l.err_off + align_up(sizeof(ff) * size_t(iters) * size_t(W / kGsMinLpc), 256);
+    l.chirp_off = l.err_off + align_up(sizeof(ff) * size_t(B) * size_t(iters) * size_t(W / kGsMinLpc), 256);
     // the chirp factors of Fresnel propagation (gs_iterate_fresnel)
     l.total = l.chirp_off + align_up(sizeof(float2) * size_t(H + W), 256);
     return l;
@@ -415,8 +444,9 @@ extern "C" int gs_workspace_size(int H, int W, int iters, int precision, size_t*
 
 namespace holo {
 
-// gs_iterate and gs_iterate_fresnel; `fresnel` selects the propagation pair
-static int gs_iterate_impl(const char* who, const float* d_target, int H, int W, int iters, int levels,
+// gs_iterate, gs_iterate_batch (B targets) and gs_iterate_fresnel; `fresnel` selects the
+// propagation pair
+static int gs_iterate_impl(const char* who, int B, const float* d_target, int H, int W, int iters, int levels,
                            const float* d_init_phase, const uint8_t* d_codes, int64_t L, int lut_levels,
                            uint64_t seed, int64_t start_index, int precision, bool fresnel, double kappa,
                            uint8_t* d_phase_codes, float* d_replay, double* d_err, const float* d_state_in,
@@ -429,12 +459,14 @@ static int gs_iterate_impl(const char* who, const float* d_target, int H, int W,
         return fail(HOLO_EINVAL, "%s: levels=%d is not a power of two in [2, 256]", who, levels);
     if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "%s: precision %d is not built", who, precision);
     if (!d_target) return fail(HOLO_EINVAL, "%s: d_target is NULL", who);
+    if (B < 1 || B > 65535 || int64_t(B) * H * W > (int64_t(1) << 31))
+        return fail(HOLO_EINVAL, "%s: %d targets of %dx%d (B*H*W at most 2^31)", who, B, H, W);
     PhaseSource ps;
     const bool use_lut = !d_init_phase && !d_state_in;
     rc = make_phase_source(who, use_lut ? d_codes : nullptr, use_lut ? L : 0, lut_levels, seed,
                            start_index, int64_t(H) * W, &ps);
     if (rc) return rc;
-    const GsLayout lay = gs_layout(H, W, iters);
+    const GsLayout lay = gs_layout(H, W, iters, B);
     if (!d_ws || ws_bytes < lay.total)
         return fail(HOLO_EWORKSPACE, "%s: workspace %zu bytes, need %zu", who, ws_bytes, lay.total);
     if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0)
@@ -455,6 +487,8 @@ static int gs_iterate_impl(const char* who, const float* d_target, int H, int W,
     a.sc = reinterpret_cast<GsScalars*>(ws + lay.sc_off);
     a.err_part = reinterpret_cast<ff*>(ws + lay.err_off);
     a.iter = 0;
+    a.iters = iters;
+    a.batch = B;
     a.codes_out = nullptr;
     a.replay_out = d_replay;
     a.state_out = reinterpret_cast<float2*>(d_state_out);
@@ -474,8 +508,8 @@ static int gs_iterate_impl(const char* who, const float* d_target, int H, int W,
     a.prep_part = reinterpret_cast<const ff*>(ws + lay.prep_off);
     {
         Launch ln("gs_prepare", st);
-        k_gs_prepare<<<kGsPrepBlocks, kGsPrepThreads, 0, st>>>(d_target, int64_t(H) * W,
-                                                               reinterpret_cast<ff*>(ws + lay.prep_off));
+        k_gs_prepare<<<dim3(kGsPrepBlocks, B), kGsPrepThreads, 0, st>>>(d_target, int64_t(H) * W,
+                                                                        reinterpret_cast<ff*>(ws + lay.prep_off));
         if ((rc = ln.done("gs_prepare launch"))) return rc;
     }
     const GsTiles tiles = gs_tiles(H, W);
@@ -491,7 +525,8 @@ static int gs_iterate_impl(const char* who, const float* d_target, int H, int W,
         const int nb = col_blocks(H, W, tiles.col_v);
         if (nb < 1) return HOLO_EUNSUPPORTED;
         Launch ln("gs_finish", st);
-        const cudaError_t le = launch_pdl(k_gs_finish, dim3(iters), dim3(32), 0, st, static_cast<const ff*>(a.err_part), nb, d_err);
+        const cudaError_t le = launch_pdl(k_gs_finish, dim3(iters, B), dim3(32), 0, st,
+                                          static_cast<const ff*>(a.err_part), nb, d_err);
         if ((rc = ln.done("gs_finish launch", le))) return rc;
     }
     if (use_lut && L > 0) {
@@ -512,9 +547,32 @@ extern "C" int gs_iterate(const float* d_target, int H, int W, int iters, int le
                           uint8_t* d_phase_codes, float* d_replay, double* d_err,
                           const float* d_state_in, float* d_state_out,
                           void* d_ws, size_t ws_bytes, holo_stream_t s) {
-    return gs_iterate_impl("gs_iterate", d_target, H, W, iters, levels, d_init_phase, d_codes, L, lut_levels, seed,
-                           start_index, precision, false, 0.0, d_phase_codes, d_replay, d_err, d_state_in,
+    return gs_iterate_impl("gs_iterate", 1, d_target, H, W, iters, levels, d_init_phase, d_codes, L, lut_levels,
+                           seed, start_index, precision, false, 0.0, d_phase_codes, d_replay, d_err, d_state_in,
                            d_state_out, d_ws, ws_bytes, s);
+}
+
+extern "C" int gs_batch_workspace_size(int B, int H, int W, int iters, int precision, size_t* bytes) {
+    clear_error();
+    if (!bytes) return fail(HOLO_EINVAL, "gs_batch_workspace_size: NULL output");
+    int rc = gs_check_shape("gs_batch_workspace_size", H, W);
+    if (rc) return rc;
+    if (iters < 1 || iters > 100000) return fail(HOLO_EINVAL, "gs_batch_workspace_size: iters=%d", iters);
+    if (B < 1 || B > 65535 || int64_t(B) * H * W > (int64_t(1) << 31))
+        return fail(HOLO_EINVAL, "gs_batch_workspace_size: %d targets of %dx%d", B, H, W);
+    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "gs_batch_workspace_size: precision %d", precision);
+    *bytes = gs_layout(H, W, iters, B).total;
+    return HOLO_OK;
+}
+
+extern "C" int gs_iterate_batch(const float* d_targets, int B, int H, int W, int iters, int levels,
+                                const float* d_init_phases, const uint8_t* d_codes, int64_t L, int lut_levels,
+                                uint64_t seed, int64_t start_index, int precision, uint8_t* d_phase_codes,
+                                float* d_replay, double* d_err, const float* d_states_in, float* d_states_out,
+                                void* d_ws, size_t ws_bytes, holo_stream_t s) {
+    return gs_iterate_impl("gs_iterate_batch", B, d_targets, H, W, iters, levels, d_init_phases, d_codes, L,
+                           lut_levels, seed, start_index, precision, false, 0.0, d_phase_codes, d_replay, d_err,
+                           d_states_in, d_states_out, d_ws, ws_bytes, s);
 }
 
 extern "C" int gs_iterate_fresnel(const float* d_target, int H, int W, int iters, int levels,
@@ -522,7 +580,7 @@ extern "C" int gs_iterate_fresnel(const float* d_target, int H, int W, int iters
                                   uint64_t seed, int64_t start_index, double kappa, uint8_t* d_phase_codes,
                                   float* d_replay, double* d_err, const float* d_state_in, float* d_state_out,
                                   void* d_ws, size_t ws_bytes, holo_stream_t s) {
-    return gs_iterate_impl("gs_iterate_fresnel", d_target, H, W, iters, levels, d_init_phase, d_codes, L,
+    return gs_iterate_impl("gs_iterate_fresnel", 1, d_target, H, W, iters, levels, d_init_phase, d_codes, L,
                            lut_levels, seed, start_index, HOLO_FP32, true, kappa, d_phase_codes, d_replay, d_err,
                            d_state_in, d_state_out, d_ws, ws_bytes, s);
 }

@@ -120,6 +120,12 @@ _SIGS = {
                                       _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
                                       _c.c_void_p, _c.c_size_t, _c.c_void_p]),
     "gs_state_phase": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_void_p]),
+    "gs_batch_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int,
+                                           _c.POINTER(_c.c_size_t)]),
+    "gs_iterate_batch": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
+                                    _c.c_void_p, _c.c_int64, _c.c_int, _c.c_uint64, _c.c_int64, _c.c_int,
+                                    _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p,
+                                    _c.c_void_p, _c.c_size_t, _c.c_void_p]),
     "ws_phase_resample": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p,
                                      _c.c_void_p]),
     "ws_adam_update": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_void_p, _c.c_int64, _c.c_float,
@@ -393,6 +399,23 @@ def gs_iterate_fresnel(d_target, H, W, iters, levels, d_init_phase, d_codes, L, 
                  _ptr(d_codes), L, lut_levels, seed, start_index, float(kappa),
                  _ptr(d_phase_codes), _ptr(d_replay), _ptr(d_err), _ptr(d_state_in),
                  _ptr(d_state_out), _ptr(d_ws), ws_bytes, _stream(stream, d_target))
+
+
+def gs_batch_workspace_size(B, H, W, iters, precision=HOLO_FP32):
+    b = ctypes.c_size_t(0)
+    _call("gs_batch_workspace_size", B, H, W, iters, precision, ctypes.byref(b))
+    return b.value
+
+
+def gs_iterate_batch(d_targets, B, H, W, iters, levels, d_init_phases, d_codes, L, lut_levels, seed,
+                     start_index, precision, d_phase_codes, d_replay, d_err, d_states_in, d_states_out,
+                     d_ws, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("gs_iterate_batch", _ptr(d_targets), B, H, W, iters, levels, _ptr(d_init_phases),
+                 _ptr(d_codes), L, lut_levels, seed, start_index, precision,
+                 _ptr(d_phase_codes), _ptr(d_replay), _ptr(d_err), _ptr(d_states_in),
+                 _ptr(d_states_out), _ptr(d_ws), ws_bytes, _stream(stream, d_targets))
 
 
 def gs_state_phase(d_state, H, W, d_phase, stream=None):
