@@ -51,10 +51,12 @@ def test_small_study_against_oracle(cuda):
     if flipped == 0:
         assert abs(g_nmse - nmse_e2e) <= NMSE_REL * nmse_e2e, (g_nmse, nmse_e2e)
     print(f"study frame: {flipped} flipped pixels, NMSE {g_nmse:.6e} vs oracle end to end {nmse_e2e:.6e}")
-    # the study's NMSE of that frame is the per-frame call's (same kernels, same inputs)
+    # the study's NMSE of that frame is the per-frame call's (same kernels, same inputs; the
+    # study re-runs the autotuner, whose choice of accumulator groups may change the
+    # float32 summation order of the replay, hence 1e-6 rather than bit equality)
     res1 = study.lut_length_study(sizes=(S,), N=N, runs=1, n_targets=1, points=2, device=cuda)
     block = res1[f"{S}x{S}"]
     r1 = {r["L"]: r for r in block["rows"]}[L]
     assert r1["std"] is None and block["unrepeated_ratio_std"] is None   # one sample: undefined
     g1 = r1["per_target"][0] * block["unrepeated_nmse"][0]
-    assert abs(g1 - g_nmse) <= 1e-12 * g_nmse, (g1, g_nmse)
+    assert abs(g1 - g_nmse) <= 1e-6 * g_nmse, (g1, g_nmse)
