@@ -618,11 +618,26 @@ def run_batch_leg(dev, stream, reps=3):
         t_graph = timed(lambda: holo.holo_graph_launch(g, s))
     finally:
         holo.holo_graph_destroy(g)
+    # the same batch as one persistent launch with its device work queue, eagerly and as a
+    # graph (counter clear + launch)
+    pws = torch.empty(holo.ospr_batch_persistent_workspace_size(arr), dtype=torch.uint8, device=dev)
+    holo.holo_tc_status(clear=True)
+    t_pers = timed(lambda: holo.ospr_generate_batch_persistent(arr, pws, stream=s))
+    pg = holo.ospr_batch_persistent_graph_create(arr, pws)
+    try:
+        t_pgraph = timed(lambda: holo.holo_graph_launch(pg, s))
+    finally:
+        holo.holo_graph_destroy(pg)
+    pers_fault = holo.holo_tc_status(clear=True)
     return {"workload": "64 frames, shapes {512^2, 1024^2, 2048^2, 1024x2048}, N in 8..32, L = 2^(10..18), "
                         "seed 42, blob targets; per frame lut_build + ospr_generate + replay_error",
             "subframes": sub, "unit": "sub-frames/s",
             "per_frame_launches": sub / (t_pf / 1e3), "batch_call": sub / (t_batch / 1e3),
-            "graph_launch": sub / (t_graph / 1e3), "ms": {"per_frame": t_pf, "batch": t_batch, "graph": t_graph},
+            "graph_launch": sub / (t_graph / 1e3),
+            "persistent": sub / (t_pers / 1e3), "persistent_graph": sub / (t_pgraph / 1e3),
+            "persistent_wait_expired": bool(pers_fault),
+            "ms": {"per_frame": t_pf, "batch": t_batch, "graph": t_graph, "persistent": t_pers,
+                   "persistent_graph": t_pgraph},
             "tuning": tunings}
 
 

@@ -364,6 +364,37 @@ int ospr_batch_graph_create(const holo_frame_desc* h_frames, int n_frames, int p
 int holo_graph_launch(holo_graph* g, holo_stream_t s);
 int holo_graph_destroy(holo_graph* g);
 
+/*
+ * ospr_generate_batch_persistent - the batch of ospr_generate_batch (table build if asked,
+ * ospr_generate and, with d_err, replay_error for every frame) as ONE persistent kernel
+ * launch with a work queue in device memory (an engineering extension, not part of the
+ * method). One 512-thread CTA per SM takes items in queue order: a table range, a column
+ * IDFT tile, a row tile, a column DFT tile, a finalize range or an error block of some
+ * frame. Dependencies between the passes of a frame are completion counters in the
+ * workspace: an item waits (thread 0 polling with acquire loads) only for items that come
+ * earlier in the queue, so the launch cannot deadlock; every wait is bounded by
+ * wait_limit_us microseconds (0: one second). When a wait expires the kernel sets the
+ * flag holo_tc_status reports, every CTA stops taking items and the call's results are not
+ * to be trusted (holo_check then returns HOLO_ETIMEOUT).
+ * Frames are spread over S workspace slots (S = 8, HOLO_BATCH_STREAMS overrides), longest
+ * first; each slot's frames run in order and the slots' items are interleaved. The tile
+ * variants are fixed at 0 and the chunking (pairs in flight, accumulator groups) is the
+ * shape's current tuning, so each frame's bits, replay and error equal those of
+ * ospr_generate + replay_error under tuning (0, 0, 0, chunk, groups) of that shape.
+ * Supports H, W in {512, 1024, 2048}, float32, frames with d_target and d_replay
+ * (HOLO_EUNSUPPORTED / HOLO_EINVAL otherwise). The workspace (caller-owned, 256-byte
+ * aligned) holds the slots, the counters, the frame table and the queue; the call writes
+ * the table and the queue (a copy ordered on s before the launch). Calls sharing a
+ * workspace must not overlap on the GPU.
+ * ospr_batch_persistent_graph_create captures the counter clear and the launch in a CUDA
+ * graph (replayed by holo_graph_launch); the queue stays in d_ws, which the graph reuses.
+ */
+int ospr_batch_persistent_workspace_size(const holo_frame_desc* h_frames, int n_frames, size_t* bytes);
+int ospr_generate_batch_persistent(const holo_frame_desc* h_frames, int n_frames, int wait_limit_us,
+                                   void* d_ws, size_t ws_bytes, holo_stream_t s);
+int ospr_batch_persistent_graph_create(const holo_frame_desc* h_frames, int n_frames, int wait_limit_us,
+                                       void* d_ws, size_t ws_bytes, holo_graph** out);
+
 /* --------------------------------------------------------------------- GS ---- */
 
 /*
@@ -560,9 +591,10 @@ int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, const void* d_i
 
 /*
  * holo_tc_status - the tcgen05 kernels (the convolutions, the DFT-32 stages of the
- * tensor-core precisions) bound every wait on their mbarriers; a wait that expires sets a
- * device flag (the convolution then skips its outputs; results of a DFT stage are not to
- * be trusted). Writes whether any flag is set to *fault (0 = never) and clears the flags
+ * tensor-core precisions) bound every wait on their mbarriers, and the persistent batch
+ * kernel every wait on a dependency counter; a wait that expires sets a device flag (the
+ * convolution then skips its outputs; results of a DFT stage or of the persistent batch
+ * are not to be trusted). Writes whether any flag is set to *fault (0 = never) and clears the flags
  * when `clear` is nonzero. Synchronous (reads device memory).
  */
 int holo_tc_status(int* fault, int clear);

@@ -194,6 +194,13 @@ struct holo_graph {
     int64_t kernels;   // kernels one launch replays (launch accounting)
 };
 
+namespace holo {
+// a holo_graph for graphs built in other translation units (the persistent batch)
+holo_graph* make_holo_graph(cudaGraph_t graph, cudaGraphExec_t exec, int device, int64_t kernels) {
+    return new holo_graph{graph, exec, device, kernels};
+}
+}  // namespace holo
+
 extern "C" int ospr_batch_workspace_size(const holo_frame_desc* h_frames, int n_frames, int precision,
                                          size_t* bytes) {
     clear_error();

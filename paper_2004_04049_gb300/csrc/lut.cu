@@ -1,7 +1,6 @@
 // lut.cu - the phase lookup table of Section 4 (a pool of L random phases generated once
 // and then drawn sequentially; 8-bit entries per Section 5.2).
-#include "fft_core.cuh"
-#include "runtime.h"
+#include "phase_source.cuh"
 
 namespace holo {
 
@@ -12,7 +11,7 @@ __global__ void k_lut_build(uint64_t seed, int64_t L, int bits, int cs_shift,
     pdl_wait();   // a previous kernel may still read the table being rewritten
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < L; k += stride) {
-        const uint32_t c = uint32_t(splitmix64_at(seed, uint64_t(k)) >> (64 - bits));
+        const uint32_t c = lut_entry(seed, uint64_t(k), bits);
         codes[k] = uint8_t(c);
         if (cs) cs[k] = __ldg(cs256 + (c << cs_shift));
     }

@@ -38,18 +38,7 @@ namespace holo {
 __global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, int W,
                                 float scale, float* __restrict__ I) {
     pdl_wait();
-    const size_t P = size_t(H) * W;
-    const size_t half = P / 2 + W;             // rows 0 .. H/2 inclusive
-    const size_t p = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (p >= half) return;
-    const int r = int(p / W), c = int(p % W);
-    const size_t pm = size_t((H - r) & (H - 1)) * W + size_t((W - c) & (W - 1));
-    if (pm < p) return;                        // the pair was taken by its partner
-    float s = 0.f;
-    for (int g = 0; g < groups; ++g) s += S[size_t(g) * P + p] + S[size_t(g) * P + pm];
-    s *= scale;
-    I[p] = s;
-    I[pm] = s;
+    ospr_finalize_pixel(S, groups, H, W, scale, I, size_t(blockIdx.x) * blockDim.x + threadIdx.x);
 }
 
 // Fresnel replay: no twin symmetry, I(k) = scale * sum_g S_g(k)

@@ -294,9 +294,10 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
     }
 }
 
+// Pass 1 on column tile `tile` (LPC/2 mirror column pairs) of field slot `slot`; every
+// thread of the CTA (ColCfg threads) calls it.
 template <int NC, int V, int PREC>
-__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
-k_ospr_col_ifft(OsprArgs a) {
+__device__ __forceinline__ void ospr_col_ifft_body(const OsprArgs& a, int tile, int slot) {
     constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R, S = col_stride<NC, V>();
     static_assert(stage_count(NC, R) > 1, "the line FFT's opening barrier guards the exchange buffer");
     extern __shared__ float2 sm[];
@@ -309,9 +310,9 @@ k_ospr_col_ifft(OsprArgs a) {
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     int c, pl;
-    mirror_column<LPC>(blockIdx.x, lc, W, c, pl);
+    mirror_column<LPC>(tile, lc, W, c, pl);
     bool single;   // uniform over the CTA
-    const int s0 = slot_subframe(a, int(blockIdx.y), single);
+    const int s0 = slot_subframe(a, slot, single);
     float2* xline = lines + pl * S;
     float2 v[R];
     if (a.ps.mode == kPhaseTable) {
@@ -333,25 +334,33 @@ k_ospr_col_ifft(OsprArgs a) {
     }
     col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
     pdl_trigger();
-    float2* z = a.zbuf + size_t(blockIdx.y) * size_t(NC) * size_t(W);
+    float2* z = a.zbuf + size_t(slot) * size_t(NC) * size_t(W);
 #pragma unroll
     for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
+}
+
+template <int NC, int V, int PREC>
+__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
+k_ospr_col_ifft(OsprArgs a) {
+    ospr_col_ifft_body<NC, V, PREC>(a, int(blockIdx.x), int(blockIdx.y));
 }
 
 // ------------------------------------------------------------------ pass 2 ----
 // FRESNEL: the row holds one sub-frame's IDFT(E); the hologram field is conj(Q) * IDFT(E),
 // binarised on its real part, and the replay transform takes h * Q.
+// Rows row0 + threadIdx.x / T of field slot `slot` (a CTA of any multiple of T threads
+// holds that many lines; the kernel below uses RowCfg's LPR lines per CTA).
 template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL>
-__device__ __forceinline__ void ospr_row_body(const OsprArgs& a) {
+__device__ __forceinline__ void ospr_row_body(const OsprArgs& a, int row0, int slot) {
     constexpr int R = RowCfg<NR, V>::R, T = NR / R;
     extern __shared__ float2 sm[];
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * RowCfg<NR, V>::LPR + line;
+    const int r = row0 + line;
     bool single;
-    const int s0 = slot_subframe(a, int(blockIdx.y), single);
+    const int s0 = slot_subframe(a, slot, single);
     const size_t P = size_t(a.H) * NR;
-    float2* z = a.zbuf + size_t(blockIdx.y) * P + size_t(r) * NR;
+    float2* z = a.zbuf + size_t(slot) * P + size_t(r) * NR;
     pdl_wait();
     float2 v[R];
 #pragma unroll
@@ -393,36 +402,45 @@ __device__ __forceinline__ void ospr_row_body(const OsprArgs& a) {
 template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL = false>
 __global__ void __launch_bounds__((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR)
 k_ospr_row(OsprArgs a) {
-    ospr_row_body<NR, V, REPLAY, PREC, FRESNEL>(a);
+    ospr_row_body<NR, V, REPLAY, PREC, FRESNEL>(a, int(blockIdx.x) * RowCfg<NR, V>::LPR, int(blockIdx.y));
 }
 
 
 // ------------------------------------------------------------------ pass 3 ----
-template <int NC, int V, int PREC>
-__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
-k_ospr_col_fft(OsprArgs a) {
+// Pass 3 on column tile `tile` for accumulator group g (pairs g, g + groups, ...).
+// `before_pair(j)` runs (uniformly over the CTA) before pair j is read and `after_read(j)`
+// once its field is in registers: the standalone kernel passes no-ops, the persistent
+// batch kernel waits for the pair's row pass and reports that its field may be reused.
+struct NoHook {
+    __device__ __forceinline__ void operator()(int) const {}
+};
+template <int NC, int V, int PREC, class Before = NoHook, class After = NoHook>
+__device__ __forceinline__ void ospr_col_fft_body(const OsprArgs& a, int tile, int g, Before before_pair = {},
+                                                  After after_read = {}) {
     constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R;
     extern __shared__ float2 sm[];
     float2* lines = sm;
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
-    const int c = blockIdx.x * LPC + lc;
+    const int c = tile * LPC + lc;
     const size_t P = size_t(NC) * W;
     pdl_wait();
     float acc[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) acc[e] = 0.f;
-    for (int j = blockIdx.y; j < a.pairs; j += a.groups) {
+    for (int j = g; j < a.pairs; j += a.groups) {
+        before_pair(j);
         const float2* z = a.zbuf + size_t(j) * P;
         float2 v[R];
 #pragma unroll
         for (int e = 0; e < R; ++e) v[e] = z[size_t(t + T * e) * W + c];
+        after_read(j);
         col_line_fft<NC, V, -1, PREC>(v, lines, lc, t, a);
 #pragma unroll
         for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
     }
     pdl_trigger();
-    float* S = a.sacc + size_t(blockIdx.y) * P;
+    float* S = a.sacc + size_t(g) * P;
 #pragma unroll
     for (int e = 0; e < R; ++e) {
         const size_t i = size_t(t + T * e) * W + c;
@@ -430,6 +448,31 @@ k_ospr_col_fft(OsprArgs a) {
     }
 }
 
+template <int NC, int V, int PREC>
+__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
+k_ospr_col_fft(OsprArgs a) {
+    ospr_col_fft_body<NC, V, PREC>(a, int(blockIdx.x), int(blockIdx.y));
+}
+
+
+// ------------------------------------------------------------------ finalize ----
+// I(k) = I(-k) = (sum_g S_g(k) + S_g(-k)) * scale for the pixel pair of thread index p:
+// p runs over the first half of the raster (rows 0 .. H/2), and the pair is written by the
+// index of the two that comes first
+__device__ __forceinline__ void ospr_finalize_pixel(const float* __restrict__ S, int groups, int H, int W,
+                                                    float scale, float* __restrict__ I, size_t p) {
+    const size_t P = size_t(H) * W;
+    const size_t half = P / 2 + W;             // rows 0 .. H/2 inclusive
+    if (p >= half) return;
+    const int r = int(p / W), c = int(p % W);
+    const size_t pm = size_t((H - r) & (H - 1)) * W + size_t((W - c) & (W - 1));
+    if (pm < p) return;                        // the pair was taken by its partner
+    float s = 0.f;
+    for (int g = 0; g < groups; ++g) s += S[size_t(g) * P + p] + S[size_t(g) * P + pm];
+    s *= scale;
+    I[p] = s;
+    I[pm] = s;
+}
 
 // pass launchers (ospr_col.cu, ospr_row.cu); `v` selects the tile variant
 int ospr_run_col_ifft(const OsprArgs& a, int v, cudaStream_t st);

@@ -22,6 +22,12 @@ struct PhaseSource {
     int cs_shift;          // 8 - bits: code -> index into the 256-entry cos/sin table
 };
 
+// table entry k: the top `bits` bits of SplitMix64 output k of stream `seed` (Section 4:
+// a pool of random phases generated once; 8-bit entries per Section 5.2)
+__device__ __forceinline__ uint8_t lut_entry(uint64_t seed, uint64_t k, int bits) {
+    return uint8_t(splitmix64_at(seed, k) >> (64 - bits));
+}
+
 struct SubframeDraw {
     uint64_t base;   // start + s*stride
     uint32_t base_mod;  // (start + s*stride) mod L (table mode)

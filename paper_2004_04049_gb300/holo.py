@@ -103,6 +103,11 @@ _SIGS = {
                                             _c.c_void_p]),
     "ospr_batch_graph_create": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
                                            _c.POINTER(_c.c_void_p)]),
+    "ospr_batch_persistent_workspace_size": (_c.c_int, [_c.c_void_p, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "ospr_generate_batch_persistent": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
+                                                  _c.c_void_p]),
+    "ospr_batch_persistent_graph_create": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
+                                                      _c.POINTER(_c.c_void_p)]),
     "holo_graph_launch": (_c.c_int, [_c.c_void_p, _c.c_void_p]),
     "holo_graph_destroy": (_c.c_int, [_c.c_void_p]),
     "ospr_autotune": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.POINTER(_c.c_double)]),
@@ -324,6 +329,28 @@ def ospr_batch_graph_create(frames, precision, d_ws, ws_bytes=None):
         ws_bytes = d_ws.numel() * d_ws.element_size()
     g = ctypes.c_void_p(0)
     _call("ospr_batch_graph_create", ctypes.cast(frames, ctypes.c_void_p), len(frames), precision,
+          _ptr(d_ws), ws_bytes, ctypes.byref(g))
+    return g.value
+
+
+def ospr_batch_persistent_workspace_size(frames):
+    b = ctypes.c_size_t(0)
+    _call("ospr_batch_persistent_workspace_size", ctypes.cast(frames, ctypes.c_void_p), len(frames), ctypes.byref(b))
+    return b.value
+
+
+def ospr_generate_batch_persistent(frames, d_ws, wait_limit_us=0, ws_bytes=None, stream=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    return _call("ospr_generate_batch_persistent", ctypes.cast(frames, ctypes.c_void_p), len(frames), wait_limit_us,
+                 _ptr(d_ws), ws_bytes, _stream(stream, d_ws))
+
+
+def ospr_batch_persistent_graph_create(frames, d_ws, wait_limit_us=0, ws_bytes=None):
+    if ws_bytes is None:
+        ws_bytes = d_ws.numel() * d_ws.element_size()
+    g = ctypes.c_void_p(0)
+    _call("ospr_batch_persistent_graph_create", ctypes.cast(frames, ctypes.c_void_p), len(frames), wait_limit_us,
           _ptr(d_ws), ws_bytes, ctypes.byref(g))
     return g.value
 

@@ -169,3 +169,96 @@ def test_batch_calls_from_two_threads(cuda):
     torch.cuda.synchronize()
     for bufs, _, _, _ in sets:
         _check(bufs, _per_frame(cuda, bufs))
+
+
+# ----------------------------------------------------------------- persistent ----
+PFRAMES = [  # H, W, N, L, seed: the shapes of the mixed batch, odd and even N, several tables
+    (512, 512, 5, 1031, 21),
+    (1024, 2048, 8, 4099, 22),
+    (2048, 512, 3, 65537, 23),
+    (1024, 1024, 24, 10007, 24),
+    (512, 1024, 1, 0, 25),
+    (2048, 2048, 4, holo.L_UNREPEATED, 26),
+    (512, 512, 33, 2 ** 18, 27),          # more pairs than one chunk: accumulation across chunks
+]
+
+
+def _pdescs(bufs, specs):
+    return holo.frame_array([holo.frame_desc(b["T"], H, W, N, b["codes"], L, 256, seed, L > 0, 0, 0,
+                                             b["bits"], b["I"], b["err"])
+                             for (H, W, N, L, seed), b in zip(specs, bufs)])
+
+
+def _pref(cuda, bufs, specs):
+    """Per-frame calls under the persistent launch's tiles: variant 0, the shape's chunking."""
+    ref = []
+    for (H, W, N, L, seed), b in zip(specs, bufs):
+        t = holo.ospr_tuning_get(H, W)
+        holo.ospr_tuning_set(H, W, 0, 0, 0, t["chunk"], t["groups"])
+        try:
+            codes = pipeline.lut(seed, L, device=cuda) if L > 0 else None
+            bits, I = pipeline.ospr(b["T"], N, codes, L, 256, seed)
+            err = pipeline.error(I, b["T"])
+            ref.append((bits.cpu().numpy(), I.cpu().numpy(), err.cpu().numpy()))
+        finally:
+            holo.ospr_tuning_set(H, W, t["col_ifft_variant"], t["col_fft_variant"], t["row_variant"], t["chunk"],
+                                 t["groups"])
+    return ref
+
+
+def test_persistent_equals_per_frame(cuda):
+    bufs = [_alloc(cuda, s, k) for k, s in enumerate(PFRAMES)]
+    arr = _pdescs(bufs, PFRAMES)
+    ws = torch.empty(holo.ospr_batch_persistent_workspace_size(arr), dtype=torch.uint8, device=cuda)
+    holo.holo_tc_status(clear=True)
+    holo.ospr_generate_batch_persistent(arr, ws)
+    torch.cuda.synchronize()
+    assert holo.holo_tc_status() == 0
+    holo.holo_check()
+    _check(bufs, _pref(cuda, bufs, PFRAMES))
+    # a second launch on the same workspace (counters cleared by the call) and the graph
+    for b in bufs:
+        b["I"].zero_()
+        b["bits"].zero_()
+        b["err"].zero_()
+    g = holo.ospr_batch_persistent_graph_create(arr, ws)
+    try:
+        for _ in range(2):
+            holo.holo_graph_launch(g)
+        torch.cuda.synchronize()
+    finally:
+        holo.holo_graph_destroy(g)
+    assert holo.holo_tc_status() == 0
+    _check(bufs, _pref(cuda, bufs, PFRAMES))
+
+
+def test_persistent_bounded_wait_expires(cuda, monkeypatch):
+    # a test hook makes the first dependency wait wait for a count nothing reaches: the wait
+    # gives up after its limit, the fault flag is set, every CTA stops, and the context
+    # stays usable
+    bufs = [_alloc(cuda, s, k) for k, s in enumerate(PFRAMES[:2])]
+    arr = _pdescs(bufs, PFRAMES[:2])
+    ws = torch.empty(holo.ospr_batch_persistent_workspace_size(arr), dtype=torch.uint8, device=cuda)
+    holo.holo_tc_status(clear=True)
+    monkeypatch.setenv("HOLO_FAULT_INJECT", "persist_wait")
+    holo.ospr_generate_batch_persistent(arr, ws, wait_limit_us=2000)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("HOLO_FAULT_INJECT")
+    assert holo.holo_tc_status() == 1
+    with pytest.raises(holo.HoloError) as ei:
+        holo.holo_check()
+    assert ei.value.status == holo.HOLO_ETIMEOUT
+    assert holo.holo_tc_status(clear=True) == 1
+    assert holo.holo_tc_status() == 0
+    holo.ospr_generate_batch_persistent(arr, ws)
+    torch.cuda.synchronize()
+    assert holo.holo_tc_status() == 0
+    _check(bufs, _pref(cuda, bufs, PFRAMES[:2]))
+
+
+def test_persistent_rejects_unsupported(cuda):
+    bufs = [_alloc(cuda, s, k) for k, s in enumerate(FRAMES[:1])]   # 128x128
+    arr = _descs(bufs)[:1]
+    with pytest.raises(holo.HoloError) as ei:
+        holo.ospr_batch_persistent_workspace_size(holo.frame_array(list(arr)))
+    assert ei.value.status == holo.HOLO_EUNSUPPORTED
