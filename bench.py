@@ -452,6 +452,32 @@ def run_ours(args):
     gsb_ips = GB * GS_ITERS * gs_runs / (gsb_ms / 1e3)
     assert torch.equal(berr[0], gerr), "batch target 0 differs from the single-target run"
 
+    # GS with the DFT-32 stages on the tensor cores (split hi/lo operands), same workload
+    gs_prec = {}
+    for pname, prec in (("fp16x2", holo.HOLO_FP16X2), ("bf16x2", holo.HOLO_BF16X2)):
+        pws = torch.empty(holo.gs_workspace_size(H, W, GS_ITERS, prec), dtype=torch.uint8, device=dev)
+        perr = torch.empty(GS_ITERS, dtype=torch.float64, device=dev)
+
+        def gs_prec_run():
+            holo.gs_iterate(targets[0], H, W, GS_ITERS, 256, None, gcodes, GS_L, 256, LUT_SEED, 0, prec,
+                            gq, gI, perr, None, None, pws, pws.numel(), stream=stream.cuda_stream)
+
+        gs_prec_run()
+        barrier()
+        pms = 0.0
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gs_prec_run()
+            e1.record(stream)
+            e1.synchronize()
+            pms += e0.elapsed_time(e1)
+        pe = perr.cpu().numpy()
+        ge = gerr.cpu().numpy()
+        gs_prec[pname] = {"value": GS_ITERS * 3 / (pms / 1e3), "unit": "iter/s",
+                          "eps20_rel_to_fp32": float(abs(pe[-1] - ge[-1]) / ge[-1])}
+
     # end to end through the public API: every frame's target copied in from page-locked
     # host memory and every frame's result copied back (the hologram bits and the error;
     # in a second measurement the replay image too), all inside one
@@ -521,6 +547,7 @@ def run_ours(args):
                    "value": gs_ips, "unit": "iter/s", "nmse_after_20": gs_nmse,
                    "bytes_per_iter_model": 36 * P,
                    "achieved_GBps": gs_ips * 36 * P / 1e9,
+                   "precision": gs_prec,
                    "batch": {"targets": GB, "value": gsb_ips, "unit": "iter/s",
                              "how": "gs_iterate_batch: every pass one launch for all targets",
                              "achieved_GBps": gsb_ips * 36 * P / 1e9,

@@ -424,6 +424,9 @@ int gs_workspace_size(int H, int W, int iters, int precision, size_t* bytes);
  *   d_err         [iters] float64 output or NULL: eps_k.
  *   d_state_in    [H][W][2] float32 (re, im) replay-plane field to resume from, or NULL.
  *   d_state_out   [H][W][2] float32 output or NULL: E after the last iteration.
+ *   precision     HOLO_FP32, or HOLO_FP16X2 / HOLO_BF16X2 (the DFT-32 stages of every line
+ *                 transform on the tensor cores with split hi/lo operands and float32
+ *                 accumulation, as in ospr_generate) for H, W in {1024, 2048}.
  * Errors: HOLO_EINVAL, HOLO_EUNSUPPORTED, HOLO_EWORKSPACE, HOLO_ECUDA.
  */
 int gs_iterate(const float* d_target, int H, int W, int iters, int levels,

@@ -24,6 +24,7 @@
 #include "fft_core.cuh"
 #include "phase_source.cuh"
 #include "runtime.h"
+#include "tc_dft.cuh"
 
 namespace holo {
 
@@ -44,6 +45,10 @@ template <> struct GsColCfg<2048, 1> { static constexpr int R = 16, LPC = 4; };
 template <> struct GsColCfg<512, 2>  { static constexpr int R = 16, LPC = 2; };
 template <> struct GsColCfg<1024, 2> { static constexpr int R = 16, LPC = 2; };
 template <> struct GsColCfg<2048, 2> { static constexpr int R = 32, LPC = 2; };
+// tensor-core precisions (variant 3): radix-32 lines, each staged in two buffers
+constexpr int kGsTcVariant = 3;
+template <> struct GsColCfg<1024, 3> { static constexpr int R = 32, LPC = 8; };
+template <> struct GsColCfg<2048, 3> { static constexpr int R = 32, LPC = 4; };
 template <int N, int V> struct GsRowCfg;
 template <> struct GsRowCfg<64, 0>   { static constexpr int R = 2,  LPR = 4; };
 template <> struct GsRowCfg<128, 0>  { static constexpr int R = 4,  LPR = 4; };
@@ -58,6 +63,8 @@ template <> struct GsRowCfg<2048, 1> { static constexpr int R = 16, LPR = 1; };
 template <> struct GsRowCfg<512, 2>  { static constexpr int R = 16, LPR = 2; };
 template <> struct GsRowCfg<1024, 2> { static constexpr int R = 8,  LPR = 2; };
 template <> struct GsRowCfg<2048, 2> { static constexpr int R = 16, LPR = 2; };
+template <> struct GsRowCfg<1024, 3> { static constexpr int R = 32, LPR = 4; };
+template <> struct GsRowCfg<2048, 3> { static constexpr int R = 32, LPR = 2; };
 constexpr bool gs_has_variants(int N) { return N >= 512 && N <= 2048; }
 constexpr int kGsMinLpc = 2;   // the smallest LPC of any variant (bounds the error partials)
 
@@ -86,6 +93,7 @@ struct GsArgs {
     float2* state_out;
     const float2* tw;
     const float2* cs256;
+    const TcFrags* tc;           // DFT-32 A fragments of the tensor-core precision in use
     float inv_sqrt_p;
     // Fresnel propagation: Q(y, x) = chirp_y[y] * chirp_x[x] (null for the far field)
     const float2* chirp_y;
@@ -94,15 +102,52 @@ struct GsArgs {
 
 template <int NC, int V>
 constexpr int gs_col_stride() { return col_line_stride(NC, GsColCfg<NC, V>::R, GsColCfg<NC, V>::LPC); }
+// the tensor-core precisions (PREC != 0) stage every line in two buffers
+constexpr int gs_nbuf(int prec) { return prec ? 2 : 1; }
 // col_init and row also hold one copy of the cos/sin table (one lookup per pixel)
-template <int NC, int V>
+template <int NC, int V, int PREC = 0>
 constexpr size_t gs_col_smem() {
-    return sizeof(float2) * (256 + size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>());
+    return sizeof(float2) * (256 + size_t(gs_nbuf(PREC)) * GsColCfg<NC, V>::LPC * gs_col_stride<NC, V>());
 }
 // the row pass looks up the quantised codes in a 16-way replicated table (conflict-free)
-template <int NR, int V>
+template <int NR, int V, int PREC = 0>
 constexpr size_t gs_row_smem() {
-    return sizeof(float2) * (kCsSmemEntries + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
+    return sizeof(float2) * (kCsSmemEntries + size_t(gs_nbuf(PREC)) * GsRowCfg<NR, V>::LPR *
+                                                  line_stride(NR, GsRowCfg<NR, V>::R));
+}
+
+// Line FFT of a GS column pass (LPC lines of T threads, lane-consecutive columns); the
+// tensor-core precisions run the DFT-32 stages on mma.sync with split hi/lo operands,
+// warp w working on line w / WPL of the second buffer set.
+template <int NC, int V, int DIR, int PREC>
+__device__ __forceinline__ void gs_col_line_fft(float2 (&v)[GsColCfg<NC, V>::R], float2* lines, int lc, int t,
+                                                const GsArgs& a) {
+    constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, S = gs_col_stride<NC, V>();
+    if constexpr (PREC == 0) {
+        line_fft<NC, R, DIR, true>(v, lines + lc * S, t, a.tw);
+    } else {
+        static_assert(R == 32 && (NC == 1024 || NC == 2048), "tensor-core stages need radix-32 lines");
+        constexpr int WPL = (NC / R) / 32;
+        float2* lines2 = lines + LPC * S;
+        const int warp = threadIdx.x >> 5;
+        const int wline = warp / WPL, wl = warp % WPL;
+        line_fft_tc<NC, DIR, PREC>(v, lines + lc * S, lines2 + lc * S, lines + wline * S, lines2 + wline * S, t, wl,
+                                   a.tc, a.tw);
+    }
+}
+// Line FFT of the GS row pass: line `line` of LPR, T threads per line
+template <int NR, int V, int DIR, int PREC>
+__device__ __forceinline__ void gs_row_line_fft(float2 (&v)[GsRowCfg<NR, V>::R], float2* lines, int line, int t,
+                                                const GsArgs& a) {
+    constexpr int R = GsRowCfg<NR, V>::R, LPR = GsRowCfg<NR, V>::LPR, T = NR / R, S = line_stride(NR, R);
+    if constexpr (PREC == 0) {
+        line_fft<NR, R, DIR, (T > 32)>(v, lines + line * S, t, a.tw);
+    } else {
+        static_assert(R == 32 && (NR == 1024 || NR == 2048), "tensor-core stages need radix-32 lines");
+        float2* lines2 = lines + LPR * S;
+        line_fft_tc<NR, DIR, PREC>(v, lines + line * S, lines2 + line * S, lines + line * S, lines2 + line * S, t,
+                                   t >> 5, a.tc, a.tw);
+    }
 }
 
 // The arguments of target b of a batch: every per-target buffer advances by b fields;
@@ -145,7 +190,7 @@ __device__ __forceinline__ float gs_scale(const ff* __restrict__ partials, int64
 }
 
 // --------------------------------------------------------------- col_init ----
-template <int NC, int V>
+template <int NC, int V, int PREC = 0>
 __global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC)
 k_gs_col_init(GsArgs a0) {
     constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
@@ -184,7 +229,7 @@ k_gs_col_init(GsArgs a0) {
             v[e] = make_float2(ts * ph.x, ts * ph.y);
         }
     }
-    line_fft<NC, R, +1, true>(v, lines + lc * gs_col_stride<NC, V>(), t, a.tw);
+    gs_col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
     pdl_trigger();
 #pragma unroll
     for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
@@ -192,12 +237,11 @@ k_gs_col_init(GsArgs a0) {
 
 // -------------------------------------------------------------------- row ----
 // FRESNEL: the hologram field is conj(Q) * IDFT(E) and the replay transform takes h * Q.
-template <int NR, int V, bool FRESNEL = false>
+template <int NR, int V, bool FRESNEL = false, int PREC = 0>
 __global__ void __launch_bounds__((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR)
 k_gs_row(GsArgs a0) {
     constexpr int R = GsRowCfg<NR, V>::R, T = NR / R;
     const GsArgs a = gs_target(a0, blockIdx.y);
-    constexpr bool BLOCK = T > 32;
     extern __shared__ float2 sm[];
     float2* cs = sm;
     float2* lines = sm + kCsSmemEntries;
@@ -207,11 +251,10 @@ k_gs_row(GsArgs a0) {
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int r = blockIdx.x * GsRowCfg<NR, V>::LPR + line;
     float2* z = a.y + size_t(r) * NR;
-    float2* buf = lines + line * line_stride(NR, R);
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
-    line_fft<NR, R, +1, BLOCK>(v, buf, t, a.tw);
+    gs_row_line_fft<NR, V, +1, PREC>(v, lines, line, t, a);
     const int levels = 1 << a.levels_bits;
     const float k_code = float(levels) * 0.15915494309189533577f;   // levels / (2 pi)
     const int shift = 8 - a.levels_bits;
@@ -230,16 +273,17 @@ k_gs_row(GsArgs a0) {
         v[e] = cs_lookup(cs, uint32_t(q) << shift);
         if constexpr (FRESNEL) v[e] = cmul(v[e], qc);
     }
-    line_fft<NR, R, -1, BLOCK>(v, buf, t, a.tw);
+    gs_row_line_fft<NR, V, -1, PREC>(v, lines, line, t, a);
     pdl_trigger();
 #pragma unroll
     for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
 }
 
 // -------------------------------------------------------------------- col ----
-template <int NC, int V, bool LAST>
+// (the tensor-core variant keeps its DFT-32 fragments in registers: one CTA per SM's share)
+template <int NC, int V, bool LAST, int PREC = 0>
 __global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC,
-                                  (NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC <= 256 ? 2 : 1)
+                                  (NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC <= 256 && PREC == 0 ? 2 : 1)
 k_gs_col(GsArgs a0) {
     constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
     const GsArgs a = gs_target(a0, blockIdx.y);
@@ -249,7 +293,6 @@ k_gs_col(GsArgs a0) {
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
-    float2* buf = lines + lc * gs_col_stride<NC, V>();
     pdl_wait();
     // the target and the scale do not depend on the transform: load them with the field
     // so that their latency hides behind the column DFT
@@ -262,7 +305,7 @@ k_gs_col(GsArgs a0) {
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = a.y[p0 + e * rs];
-    line_fft<NC, R, -1, true>(v, buf, t, a.tw);
+    gs_col_line_fft<NC, V, -1, PREC>(v, lines, lc, t, a);
     float err = 0.f;
 #pragma unroll
     for (int e = 0; e < R; ++e) {
@@ -289,7 +332,7 @@ k_gs_col(GsArgs a0) {
     if (threadIdx.x == 0)
         a.err_part[(size_t(blockIdx.y) * a.iters + size_t(a.iter)) * gridDim.x + blockIdx.x] = b[0];
     if constexpr (!LAST) {
-        line_fft<NC, R, +1, true>(v, buf, t, a.tw);
+        gs_col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
         pdl_trigger();
 #pragma unroll
         for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
@@ -328,25 +371,25 @@ static GsTiles gs_tiles(int H, int W) {
 }
 
 // every launch after k_gs_prepare may overlap the previous kernel's tail (pdl_wait first)
-template <int NC, int V>
+template <int NC, int V, int PREC = 0>
 static int launch_col_init(const GsArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
-    constexpr size_t smem = gs_col_smem<NC, V>();
-    int rc = ensure_smem((const void*)k_gs_col_init<NC, V>, smem, &mask);
+    constexpr size_t smem = gs_col_smem<NC, V, PREC>();
+    int rc = ensure_smem((const void*)k_gs_col_init<NC, V, PREC>, smem, &mask);
     if (rc) return rc;
     Launch ln("gs_col_init", st);
-    const cudaError_t le = launch_pdl(k_gs_col_init<NC, V>, dim3(a.W / GsColCfg<NC, V>::LPC, a.batch),
+    const cudaError_t le = launch_pdl(k_gs_col_init<NC, V, PREC>, dim3(a.W / GsColCfg<NC, V>::LPC, a.batch),
                                       dim3((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC), smem, st, a);
     return ln.done("gs_col_init launch", le);
 }
-template <int NR, int V, bool FRESNEL>
+template <int NR, int V, bool FRESNEL, int PREC = 0>
 static int launch_row_kind(const GsArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
-    constexpr size_t smem = gs_row_smem<NR, V>();
-    int rc = ensure_smem((const void*)k_gs_row<NR, V, FRESNEL>, smem, &mask);
+    constexpr size_t smem = gs_row_smem<NR, V, PREC>();
+    int rc = ensure_smem((const void*)k_gs_row<NR, V, FRESNEL, PREC>, smem, &mask);
     if (rc) return rc;
     Launch ln("gs_row", st);
-    const cudaError_t le = launch_pdl(k_gs_row<NR, V, FRESNEL>, dim3(a.H / GsRowCfg<NR, V>::LPR, a.batch),
+    const cudaError_t le = launch_pdl(k_gs_row<NR, V, FRESNEL, PREC>, dim3(a.H / GsRowCfg<NR, V>::LPR, a.batch),
                                       dim3((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR), smem, st, a);
     return ln.done("gs_row launch", le);
 }
@@ -354,19 +397,43 @@ template <int NR, int V>
 static int launch_row(const GsArgs& a, cudaStream_t st) {
     return a.chirp_y ? launch_row_kind<NR, V, true>(a, st) : launch_row_kind<NR, V, false>(a, st);
 }
-template <int NC, int V>
+template <int NC, int V, int PREC = 0>
 static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
     static uint64_t mask0 = 0, mask1 = 0;
-    constexpr size_t smem = sizeof(float2) * size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>();
+    constexpr size_t smem = sizeof(float2) * size_t(gs_nbuf(PREC)) * GsColCfg<NC, V>::LPC * gs_col_stride<NC, V>();
     const dim3 grid(a.W / GsColCfg<NC, V>::LPC, a.batch), threads((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC);
-    int rc = last ? ensure_smem((const void*)k_gs_col<NC, V, true>, smem, &mask1)
-                  : ensure_smem((const void*)k_gs_col<NC, V, false>, smem, &mask0);
+    int rc = last ? ensure_smem((const void*)k_gs_col<NC, V, true, PREC>, smem, &mask1)
+                  : ensure_smem((const void*)k_gs_col<NC, V, false, PREC>, smem, &mask0);
     if (rc) return rc;
     Launch ln("gs_col", st);
-    const cudaError_t le = last ? launch_pdl(k_gs_col<NC, V, true>, grid, threads, smem, st, a)
-                                : launch_pdl(k_gs_col<NC, V, false>, grid, threads, smem, st, a);
+    const cudaError_t le = last ? launch_pdl(k_gs_col<NC, V, true, PREC>, grid, threads, smem, st, a)
+                                : launch_pdl(k_gs_col<NC, V, false, PREC>, grid, threads, smem, st, a);
     return ln.done("gs_col launch", le);
 }
+
+// tensor-core precisions: lengths 1024 and 2048, tile variant 3, far field only
+#define HOLO_GS_TC(n, prec, F)                                                              \
+    switch (n) {                                                                            \
+        case 1024: return prec == HOLO_BF16X2 ? F(1024, kTcBf16) : F(1024, kTcFp16);        \
+        case 2048: return prec == HOLO_BF16X2 ? F(2048, kTcBf16) : F(2048, kTcFp16);        \
+        default: return fail(HOLO_EUNSUPPORTED, "tensor-core GS: line length %d", n);     \
+    }
+static int run_col_init_tc(const GsArgs& a, int prec, cudaStream_t st) {
+#define C(n, p) launch_col_init<n, kGsTcVariant, p>(a, st)
+    HOLO_GS_TC(a.H, prec, C)
+#undef C
+}
+static int run_row_tc(const GsArgs& a, int prec, cudaStream_t st) {
+#define C(n, p) launch_row_kind<n, kGsTcVariant, false, p>(a, st)
+    HOLO_GS_TC(a.W, prec, C)
+#undef C
+}
+static int run_col_tc(const GsArgs& a, int prec, bool last, cudaStream_t st) {
+#define C(n, p) launch_col<n, kGsTcVariant, p>(a, last, st)
+    HOLO_GS_TC(a.H, prec, C)
+#undef C
+}
+static bool gs_tc_shape(int H, int W) { return (H == 1024 || H == 2048) && (W == 1024 || W == 2048); }
 
 #define HOLO_GS_V(n, v, F) (v == 2 ? F(n, 2) : v == 1 ? F(n, 1) : F(n, 0))
 #define HOLO_GS_SWITCH(n, v, F)                           \
@@ -437,7 +504,10 @@ extern "C" int gs_workspace_size(int H, int W, int iters, int precision, size_t*
     int rc = gs_check_shape("gs_workspace_size", H, W);
     if (rc) return rc;
     if (iters < 1 || iters > 100000) return fail(HOLO_EINVAL, "gs_workspace_size: iters=%d", iters);
-    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "gs_workspace_size: precision %d", precision);
+    if (precision != HOLO_FP32 && precision != HOLO_FP16X2 && precision != HOLO_BF16X2)
+        return fail(HOLO_EINVAL, "gs_workspace_size: unknown precision %d", precision);
+    if (precision != HOLO_FP32 && !gs_tc_shape(H, W))
+        return fail(HOLO_EUNSUPPORTED, "gs_workspace_size: tensor-core precisions need H, W in {1024, 2048}");
     *bytes = gs_layout(H, W, iters).total;
     return HOLO_OK;
 }
@@ -457,7 +527,10 @@ static int gs_iterate_impl(const char* who, int B, const float* d_target, int H,
     if (iters < 1 || iters > 100000) return fail(HOLO_EINVAL, "%s: iters=%d out of [1, 100000]", who, iters);
     if (!is_pow2(levels) || levels < 2 || levels > 256)
         return fail(HOLO_EINVAL, "%s: levels=%d is not a power of two in [2, 256]", who, levels);
-    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "%s: precision %d is not built", who, precision);
+    if (precision != HOLO_FP32 && precision != HOLO_FP16X2 && precision != HOLO_BF16X2)
+        return fail(HOLO_EINVAL, "%s: unknown precision %d", who, precision);
+    if (precision != HOLO_FP32 && (fresnel || !gs_tc_shape(H, W)))
+        return fail(HOLO_EUNSUPPORTED, "%s: tensor-core precisions need the far field and H, W in {1024, 2048}", who);
     if (!d_target) return fail(HOLO_EINVAL, "%s: d_target is NULL", who);
     if (B < 1 || B > 65535 || int64_t(B) * H * W > (int64_t(1) << 31))
         return fail(HOLO_EINVAL, "%s: %d targets of %dx%d (B*H*W at most 2^31)", who, B, H, W);
@@ -494,6 +567,7 @@ static int gs_iterate_impl(const char* who, int B, const float* d_target, int H,
     a.state_out = reinterpret_cast<float2*>(d_state_out);
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
+    a.tc = tab.tc[precision];
     a.inv_sqrt_p = float(1.0 / std::sqrt(double(H) * double(W)));
     a.chirp_y = a.chirp_x = nullptr;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
@@ -513,16 +587,18 @@ static int gs_iterate_impl(const char* who, int B, const float* d_target, int H,
         if ((rc = ln.done("gs_prepare launch"))) return rc;
     }
     const GsTiles tiles = gs_tiles(H, W);
-    if ((rc = run_col_init(a, tiles.col_v, st))) return rc;
+    const bool tc = precision != HOLO_FP32;
+    if ((rc = tc ? run_col_init_tc(a, precision, st) : run_col_init(a, tiles.col_v, st))) return rc;
     for (int k = 0; k < iters; ++k) {
         const bool last = k == iters - 1;
         a.iter = k;
         a.codes_out = last ? d_phase_codes : nullptr;
-        if ((rc = run_row(a, tiles.row_v, st))) return rc;
-        if ((rc = run_col(a, tiles.col_v, last, st))) return rc;
+        if ((rc = tc ? run_row_tc(a, precision, st) : run_row(a, tiles.row_v, st))) return rc;
+        if ((rc = tc ? run_col_tc(a, precision, last, st) : run_col(a, tiles.col_v, last, st))) return rc;
     }
     if (d_err) {
-        const int nb = col_blocks(H, W, tiles.col_v);
+        const int nb = tc ? W / (H == 1024 ? GsColCfg<1024, kGsTcVariant>::LPC : GsColCfg<2048, kGsTcVariant>::LPC)
+                          : col_blocks(H, W, tiles.col_v);
         if (nb < 1) return HOLO_EUNSUPPORTED;
         Launch ln("gs_finish", st);
         const cudaError_t le = launch_pdl(k_gs_finish, dim3(iters, B), dim3(32), 0, st,
@@ -560,7 +636,10 @@ extern "C" int gs_batch_workspace_size(int B, int H, int W, int iters, int preci
     if (iters < 1 || iters > 100000) return fail(HOLO_EINVAL, "gs_batch_workspace_size: iters=%d", iters);
     if (B < 1 || B > 65535 || int64_t(B) * H * W > (int64_t(1) << 31))
         return fail(HOLO_EINVAL, "gs_batch_workspace_size: %d targets of %dx%d", B, H, W);
-    if (precision != HOLO_FP32) return fail(HOLO_EUNSUPPORTED, "gs_batch_workspace_size: precision %d", precision);
+    if (precision != HOLO_FP32 && precision != HOLO_FP16X2 && precision != HOLO_BF16X2)
+        return fail(HOLO_EINVAL, "gs_batch_workspace_size: unknown precision %d", precision);
+    if (precision != HOLO_FP32 && !gs_tc_shape(H, W))
+        return fail(HOLO_EUNSUPPORTED, "gs_batch_workspace_size: tensor-core precisions need H, W in {1024, 2048}");
     *bytes = gs_layout(H, W, iters, B).total;
     return HOLO_OK;
 }

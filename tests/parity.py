@@ -63,21 +63,32 @@ def check_nmse(gpu, oracle):
     return rel
 
 
-def check_codes(gpu_q, oracle_q, oracle_H, levels):
-    """GS phase-code parity (see module docstring)."""
+# GS codes under the tensor-core precisions: the split hi/lo operands carry about 16
+# (bf16 x 2) or 22 (fp16 x 2) significant bits, so one line transform errs by a few 1e-6
+# of rms|H| (OSPR replay measured 6.4e-6 and 2.7e-6 relative) and four of them precede
+# the quantiser: a phase error of about 3e-5 rms|H| / |H_p| rad, 1.2e-3 code units at
+# |H_p| = rms|H|. The tie band is widened to 5e-3 weighted code units (4x that) and the
+# agreement floor to 99.9%, which that error rate meets with a wide margin.
+CODE_TIE_TC = 5e-3
+BIT_AGREE_TC = 0.999
+
+
+def check_codes(gpu_q, oracle_q, oracle_H, levels, tie=CODE_TIE, agree_floor=BIT_AGREE):
+    """GS phase-code parity (see module docstring); `tie` and `agree_floor` default to the
+    float32 bounds."""
     g = np.asarray(gpu_q).astype(np.int64).reshape(-1)
     o = np.asarray(oracle_q).astype(np.int64).reshape(-1)
     Hf = np.asarray(oracle_H).reshape(-1)
     diff = g != o
     agree = 1.0 - diff.mean()
-    assert agree >= BIT_AGREE, f"phase-code agreement {agree:.6f}"
+    assert agree >= agree_floor, f"phase-code agreement {agree:.6f}"
     if diff.any():
         x = levels * np.angle(Hf[diff]) / (2 * np.pi) + 0.5
         dist = np.abs(x - np.round(x))                  # distance to a decision boundary
         rms = np.sqrt(np.mean(np.abs(Hf) ** 2))
         weighted = dist * np.abs(Hf[diff]) / rms
         small = np.abs(Hf[diff]) < RE_TIE * np.abs(Hf).max()
-        ok = (weighted < CODE_TIE) | small
+        ok = (weighted < tie) | small
         assert ok.all(), f"{(~ok).sum()} code(s) differ away from a boundary (max weighted dist {weighted.max():.3e})"
         cyc = np.minimum((g[diff] - o[diff]) % levels, (o[diff] - g[diff]) % levels)
         assert cyc.max() <= 1

@@ -14,7 +14,7 @@ from oracle import fft as offt
 from oracle import gs as ogs
 from oracle import lut as olut
 from paper_2004_04049_gb300 import holo, pipeline
-from parity import NMSE_REL, REPLAY_REL, check_codes, check_replay
+from parity import BIT_AGREE_TC, CODE_TIE_TC, NMSE_REL, REPLAY_REL, check_codes, check_replay
 from synthetic import blob_target, noise_target
 
 pytestmark = pytest.mark.gpu
@@ -45,12 +45,37 @@ def test_tile_variants_parity(cuda, H, W, tiles):
         holo.gs_tuning_set(H, W)
 
 
-def _single_iteration(cuda, H, W, levels, kind):
+@pytest.mark.parametrize("H,W", [(1024, 1024), (1024, 2048), (2048, 1024)])
+@pytest.mark.parametrize("prec", [holo.HOLO_FP16X2, holo.HOLO_BF16X2])
+def test_single_iteration_parity_tensor_core(cuda, H, W, prec):
+    # the DFT-32 stages on the tensor cores with split hi/lo operands: codes against the
+    # widened tie band of parity.py, replay, error and next state against the float32 bounds
+    _single_iteration(cuda, H, W, 256, "noise", precision=prec)
+
+
+def test_tensor_core_trajectory_tracks_fp32(cuda):
+    # 20 iterations from the LUT start: the error trajectory of each tensor-core precision
+    # stays non-increasing and within the 5% drift bound that float32 keeps against the
+    # oracle (a code that ties differently parts the trajectories)
+    H = W = 1024
+    T = torch.from_numpy(blob_target(H, W, 1015)).to(cuda)
+    codes = pipeline.lut(5, 10007, device=cuda)
+    ref = pipeline.gs(T, 20, 256, codes, 10007, 256, 5)["err"].cpu().numpy()
+    for prec in (holo.HOLO_FP16X2, holo.HOLO_BF16X2):
+        e = pipeline.gs(T, 20, 256, codes, 10007, 256, 5, precision=prec)["err"].cpu().numpy()
+        assert np.all(np.diff(e) <= 1e-5 * e[0]), prec
+        assert np.all(np.abs(e - ref) <= 0.05 * ref), (prec, np.abs(e - ref).max() / ref.max())
+    with pytest.raises(holo.HoloError) as ei:
+        pipeline.gs(torch.zeros((512, 512), device=cuda), 1, 256, precision=holo.HOLO_BF16X2)
+    assert ei.value.status == holo.HOLO_EUNSUPPORTED
+
+
+def _single_iteration(cuda, H, W, levels, kind, precision=holo.HOLO_FP32):
     T = blob_target(H, W, 1010) if kind == "blob" else noise_target(H, W, 2010)
     E32 = _init_state(T, 10007, 3)
     t = torch.from_numpy(T).to(cuda)
     st = torch.from_numpy(np.stack([E32.real, E32.imag], -1).astype(np.float32)).to(cuda)
-    out = pipeline.gs(t, 1, levels, state_in=st, want_state=True)
+    out = pipeline.gs(t, 1, levels, state_in=st, want_state=True, precision=precision)
     torch.cuda.synchronize()
     gq = out["codes"].cpu().numpy()
     gI = out["replay"].cpu().numpy()
@@ -59,7 +84,10 @@ def _single_iteration(cuda, H, W, levels, kind):
     E = E32.astype(np.complex128)
     Hf = offt.ifft2(E)
     oq = ogs.quantise_phase(Hf, levels)
-    check_codes(gq, oq, Hf, levels)
+    if precision == holo.HOLO_FP32:
+        check_codes(gq, oq, Hf, levels)
+    else:
+        check_codes(gq, oq, Hf, levels, tie=CODE_TIE_TC, agree_floor=BIT_AGREE_TC)
     # stage-wise: the oracle continues from the GPU's codes
     Ts = ogs.energy_scaled_target(T)
     R = offt.fft2(ogs.hologram_of_codes(gq.astype(np.int64), levels))
