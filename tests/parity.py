@@ -90,6 +90,7 @@ def check_codes(gpu_q, oracle_q, oracle_H, levels, tie=CODE_TIE, agree_floor=BIT
         small = np.abs(Hf[diff]) < RE_TIE * np.abs(Hf).max()
         ok = (weighted < tie) | small
         assert ok.all(), f"{(~ok).sum()} code(s) differ away from a boundary (max weighted dist {weighted.max():.3e})"
+        # away from |H| ~ 0, where the phase itself is undetermined, codes differ by one level
         cyc = np.minimum((g[diff] - o[diff]) % levels, (o[diff] - g[diff]) % levels)
-        assert cyc.max() <= 1
+        assert np.all(cyc[~small] <= 1)
     return agree
