@@ -1135,6 +1135,36 @@ def run_case(name):
                 pipeline.ospr(T, N_SF, codes, GS_L, 256, LUT_SEED, precision=prec)
         torch.cuda.synchronize()
         print("case tc ok, tcgen05 fault flag", holo.holo_tc_status())
+    elif name == "infer":
+        # the learned warm start's inference at batch 1 on a 1024x1024 target, three times
+        from paper_2004_04049_gb300 import holo
+        net = holo.ws_net_create(11, 1)
+        try:
+            big = torch.from_numpy(blob_target(1024, 1024, 5)).to(dev)
+            ph = torch.empty((1024, 1024), dtype=torch.float32, device=dev)
+            for _ in range(3):
+                holo.ws_infer(net, big, 1024, 1024, ph)
+            torch.cuda.synchronize()
+        finally:
+            holo.ws_net_destroy(net)
+        print("case infer ok, max |phase|", float(ph.abs().max()))
+    elif name == "persistent":
+        # four 1024x1024 frames (N=24, L=10007) as one persistent launch, twice
+        from paper_2004_04049_gb300 import holo
+        codes = pipeline.lut(LUT_SEED, GS_L, device=dev)
+        bufs = []
+        for k in range(4):
+            bufs.append({"T": torch.from_numpy(blob_target(H, W, 1000 + k)).to(dev),
+                         "bits": torch.empty((N_SF, H * W // 32), dtype=torch.int32, device=dev),
+                         "I": torch.empty((H, W), dtype=torch.float32, device=dev),
+                         "err": torch.empty(3, dtype=torch.float64, device=dev)})
+        arr = holo.frame_array([holo.frame_desc(b["T"], H, W, N_SF, codes, GS_L, 256, LUT_SEED, False, 0, 0,
+                                                b["bits"], b["I"], b["err"]) for b in bufs])
+        pws = torch.empty(holo.ospr_batch_persistent_workspace_size(arr), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            holo.ospr_generate_batch_persistent(arr, pws)
+        torch.cuda.synchronize()
+        print("case persistent ok, wait expired", holo.holo_tc_status(clear=True))
     else:
         raise SystemExit(f"unknown case {name!r}")
 
