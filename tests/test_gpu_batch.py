@@ -262,3 +262,31 @@ def test_persistent_rejects_unsupported(cuda):
     with pytest.raises(holo.HoloError) as ei:
         holo.ospr_batch_persistent_workspace_size(holo.frame_array(list(arr)))
     assert ei.value.status == holo.HOLO_EUNSUPPORTED
+
+
+def test_persistent_frames_without_error_or_bits(cuda):
+    # frames that ask for no error (done after their last finalize item) and no bits,
+    # following a frame on the same workspace slot (one slot: every frame waits for the
+    # previous one), against the per-frame kernels under the same tiles
+    specs = [(1024, 512, 6, 4099, 31), (512, 512, 3, 1031, 32), (512, 1024, 4, 0, 33)]
+    bufs = [_alloc(cuda, s, k + 40) for k, s in enumerate(specs)]
+    arr = holo.frame_array([holo.frame_desc(b["T"], H, W, N, b["codes"], L, 256, seed, L > 0, 0, 0,
+                                            b["bits"] if k != 1 else None, b["I"], b["err"] if k != 0 else None)
+                            for k, ((H, W, N, L, seed), b) in enumerate(zip(specs, bufs))])
+    import os
+    os.environ["HOLO_BATCH_STREAMS"] = "1"
+    try:
+        ws = torch.empty(holo.ospr_batch_persistent_workspace_size(arr), dtype=torch.uint8, device=cuda)
+        holo.holo_tc_status(clear=True)
+        holo.ospr_generate_batch_persistent(arr, ws)
+        torch.cuda.synchronize()
+    finally:
+        del os.environ["HOLO_BATCH_STREAMS"]
+    assert holo.holo_tc_status() == 0
+    ref = _pref(cuda, bufs, specs)
+    for k, (b, r) in enumerate(zip(bufs, ref)):
+        assert np.array_equal(b["I"].cpu().numpy(), r[1]), k
+        if k != 1:
+            assert np.array_equal(b["bits"].cpu().numpy(), r[0]), k
+        if k != 0:
+            assert np.array_equal(b["err"].cpu().numpy(), r[2]), k
