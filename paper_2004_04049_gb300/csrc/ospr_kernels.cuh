@@ -217,11 +217,13 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
         if constexpr (MODE == kPhaseTable) {
             const uint32_t jm0 = (e == 0 && t == 0) ? z0 : m0;
             const uint32_t jm1 = (e == 0 && t == 0) ? z1 : m1;
-            uint32_t w = __ldg(a.ps.codes + i0);
+            // ordinary (coherent) loads: the persistent batch kernel builds a frame's table in
+            // the same launch that reads it, which the read-only path does not allow
+            uint32_t w = a.ps.codes[i0];
             if constexpr (!SINGLE) {
-                w |= uint32_t(__ldg(a.ps.codes + jm0)) << 8;
-                w |= uint32_t(__ldg(a.ps.codes + i1)) << 16;
-                w |= uint32_t(__ldg(a.ps.codes + jm1)) << 24;
+                w |= uint32_t(a.ps.codes[jm0]) << 8;
+                w |= uint32_t(a.ps.codes[i1]) << 16;
+                w |= uint32_t(a.ps.codes[jm1]) << 24;
             }
             i0 += D; i0 -= (i0 >= L) ? L : 0u;
             i1 += D; i1 -= (i1 >= L) ? L : 0u;

@@ -42,7 +42,7 @@ __device__ __forceinline__ SubframeDraw subframe_draw(const PhaseSource& ps, int
 
 // code of draw base + p; p < 2^24 and base_mod < 2^31 keep the table index sum in 32 bits
 __device__ __forceinline__ uint32_t draw_code(const PhaseSource& ps, const SubframeDraw& d, uint32_t p) {
-    if (ps.mode == kPhaseTable) return __ldg(ps.codes + fastmod_u32(d.base_mod + p, ps.fm, ps.L));
+    if (ps.mode == kPhaseTable) return ps.codes[fastmod_u32(d.base_mod + p, ps.fm, ps.L)];
     if (ps.mode == kPhaseGenerator) return uint32_t(splitmix64_at(ps.seed, d.base + p) >> (64 - ps.bits));
     return 0u;
 }
