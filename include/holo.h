@@ -385,7 +385,8 @@ int holo_graph_destroy(holo_graph* g);
  * (HOLO_EUNSUPPORTED / HOLO_EINVAL otherwise). The workspace (caller-owned, 256-byte
  * aligned) holds the slots, the counters, the frame table and the queue; the call writes
  * the table and the queue (a copy ordered on s before the launch). Calls sharing a
- * workspace must not overlap on the GPU.
+ * workspace must not overlap on the GPU, and frames that build their table (build_lut)
+ * must not share its buffer with another frame of the batch.
  * ospr_batch_persistent_graph_create captures the counter clear and the launch in a CUDA
  * graph (replayed by holo_graph_launch); the queue stays in d_ws, which the graph reuses.
  */
