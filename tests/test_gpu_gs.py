@@ -175,3 +175,32 @@ def test_caller_phase_equals_lut_phase(cuda, start):
     b = pipeline.gs(t, 1, 256, init_phase=torch.from_numpy(theta.astype(np.float32)).to(cuda))
     qa, qb = a["codes"].cpu().numpy(), b["codes"].cpu().numpy()
     assert np.mean(qa == qb) >= 0.9999
+
+
+def test_bench_configuration_trajectory(cuda):
+    # the GS leg of the benchmark as it runs there: 1024x1024 blob target (seed 1000),
+    # 20 iterations, 256 levels, LUT start (L = 10007, seed 7); the error trajectory against
+    # the oracle's, and the last iteration's codes and replay stage-wise from the GPU's
+    # own state before it
+    H = W = 1024
+    T = blob_target(H, W, 1000)
+    L, seed, iters = 10007, 7, 20
+    t = torch.from_numpy(T).to(cuda)
+    codes = pipeline.lut(seed, L, device=cuda)
+    out = pipeline.gs(t, iters, 256, codes, L, 256, seed)
+    geps = out["err"].cpu().numpy()
+    assert np.all(np.diff(geps) <= 1e-5 * geps[0])
+    table = olut.lut_codes(seed, L)
+    _, _, oeps, _ = ogs.gs(T, iters, table, L, seed)
+    drift = np.abs(geps - oeps) / oeps
+    assert drift[0] < 1e-4 and drift.max() < 0.05, drift
+    # stage-wise last iteration: 19 iterations on the GPU, then one more from that state
+    st19 = pipeline.gs(t, iters - 1, 256, codes, L, 256, seed, want_state=True)["state"]
+    last = pipeline.gs(t, 1, 256, state_in=st19)
+    torch.cuda.synchronize()
+    s = st19.cpu().numpy().astype(np.float64)
+    Hf = offt.ifft2(s[..., 0] + 1j * s[..., 1])
+    check_codes(last["codes"].cpu().numpy(), ogs.quantise_phase(Hf, 256), Hf, 256)
+    assert torch.equal(last["codes"], out["codes"])
+    R = offt.fft2(ogs.hologram_of_codes(last["codes"].cpu().numpy().astype(np.int64), 256))
+    check_replay(last["replay"].cpu().numpy(), np.abs(R) ** 2)
