@@ -176,14 +176,10 @@ static OsprPlan ospr_plan_with(int H, int W, int N, const OsprTuning& t) {
 
 static bool tc_shape(int H, int W) { return (H == 1024 || H == 2048) && (W == 1024 || W == 2048); }
 
-// tensor-core precisions use fixed tile variants (radix-32 lines in two buffers)
+// the tensor-core precisions run the fixed tiles of ospr_tc.cu; the tile variants of the
+// plan apply to the float32 passes
 static OsprPlan ospr_plan(int H, int W, int N, int precision = HOLO_FP32) {
-    OsprTuning t = tuning_for(H, W);
-    if (precision != HOLO_FP32) {
-        t.ci_v = t.cf_v = kTcColVariant;
-        t.row_v = kTcRowVariant;
-    }
-    OsprPlan pl = ospr_plan_with(H, W, N, t);
+    OsprPlan pl = ospr_plan_with(H, W, N, tuning_for(H, W));
     pl.prec = precision;
     return pl;
 }

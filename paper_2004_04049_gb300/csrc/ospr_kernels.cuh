@@ -480,11 +480,9 @@ __device__ __forceinline__ void ospr_finalize_pixel(const float* __restrict__ S,
 int ospr_run_col_ifft(const OsprArgs& a, int v, cudaStream_t st);
 int ospr_run_col_fft(const OsprArgs& a, int v, cudaStream_t st);
 int ospr_run_row(const OsprArgs& a, int v, bool replay, cudaStream_t st);
-// tensor-core precisions (ospr_tc.cu): lengths 1024 and 2048, fixed tile variants
+// tensor-core precisions (ospr_tc.cu, tcgen05): lengths 1024 and 2048, fixed tiles
 int ospr_run_col_ifft_tc(const OsprArgs& a, int prec, cudaStream_t st);
 int ospr_run_col_fft_tc(const OsprArgs& a, int prec, cudaStream_t st);
 int ospr_run_row_tc(const OsprArgs& a, int prec, bool replay, cudaStream_t st);
-constexpr int kTcColVariant = 1;
-constexpr int kTcRowVariant = 0;
 
 }  // namespace holo

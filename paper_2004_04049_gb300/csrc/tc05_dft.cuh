@@ -1,5 +1,5 @@
 // tc05_dft.cuh - radix-32 DFT stages of a line FFT on the 5th-generation tensor cores
-// (tcgen05.mma, accumulator in tensor memory), for the column passes of 1024-point lines.
+// (tcgen05.mma, accumulator in tensor memory), for lines of 1024 and 2048 points.
 //
 // Each thread holds one 32-point sub-line of a Stockham stage in registers (the layout of
 // fft_core.cuh). In real form the 32-point DFT is a 64x64 matrix acting on
@@ -141,6 +141,9 @@ __device__ __forceinline__ void dft32_tc05(float2 (&u)[32], Tc05Group& g, float 
     }
     if (!tc05_wait(g.bar, g.phase)) atomicExch(g.fault, 1);
     g.phase ^= 1u;
+    // the lanes leave the polling loop independently; tcgen05.ld is .sync.aligned and
+    // must be executed by the whole warp together
+    __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t taddr = g.tmem + (uint32_t(32 * ((threadIdx.x >> 5) & 3)) << 16);
     uint32_t r[32];
@@ -168,27 +171,38 @@ __device__ __forceinline__ void dft32_tc05(float2 (&u)[32], Tc05Group& g, float 
     __syncthreads();
 }
 
-// 1024-point line FFT (two radix-32 stages) of a line held by its 32 threads in canonical
-// layout (slot e <-> element t + 32 e), both stages on the tensor cores; `buf` is the
-// line's padded buffer (fft_core.cuh) for the exchange between the stages. Every thread
-// of the block calls it.
-template <int DIR, int PREC>
-__device__ __forceinline__ void line_fft_1024_tc05(float2 (&v)[32], float2* buf, int t, const float2* __restrict__ tw,
-                                                  Tc05Group& g) {
+// N-point line FFT (N = 1024 or 2048) of a line held by its T = N/32 threads in canonical
+// layout (slot e <-> element t + T e): the two radix-32 stages on the tensor cores, the
+// closing radix-2 stage of a 2048-point line on the CUDA cores. `buf` is the line's padded
+// buffer (fft_core.cuh) for the exchanges between the stages. Every thread of the block
+// calls it.
+template <int N, int DIR, int PREC>
+__device__ __forceinline__ void line_fft_tc05(float2 (&v)[32], float2* buf, int t, const float2* __restrict__ tw,
+                                             Tc05Group& g) {
+    static_assert(N == 1024 || N == 2048, "tcgen05 line FFT: 1024 or 2048 points");
+    constexpr int T = N / 32;
     const float scale = PREC == 1 ? 1.f / 256.f : 1.f;
     const float unscale = PREC == 1 ? 256.f : 1.f;
-    // stage 0 (sub-transform length 1): DFT of elements t + 32 m, output m to 32 t + m
+    // stage 0 (sub-transform length 1): DFT of elements t + T m, output m to 32 t + m
     dft32_tc05<PREC>(v, g, scale, unscale);
 #pragma unroll
     for (int m = 0; m < 32; ++m) buf[pad_index<32>(32 * t + m)] = v[m];
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = buf[pad_index<32>(t + 32 * e)];
-    // stage 1: twiddle W_1024^(t m), DFT, output m to element t + 32 m (canonical)
-    const float2* tws = tw + stage_offset(1024, 32, 1) + t;
+    for (int e = 0; e < 32; ++e) v[e] = buf[pad_index<32>(t + T * e)];
+    // stage 1 (sub-transform length 32): twiddle W_1024^(k m) with k = t mod 32, DFT,
+    // output m to element (t / 32) 1024 + k + 32 m
+    const int k = t & 31;
+    const float2* tws = tw + stage_offset(N, 32, 1) + k;
 #pragma unroll
     for (int m = 1; m < 32; ++m) v[m] = cmul_dir<DIR>(v[m], __ldg(tws + 32 * m));
     dft32_tc05<PREC>(v, g, scale, unscale);
+    if constexpr (N == 2048) {
+        // dft32_tc05 ends with a block barrier, so the buffer is free again
+#pragma unroll
+        for (int m = 0; m < 32; ++m) buf[pad_index<32>((t >> 5) * 1024 + k + 32 * m)] = v[m];
+        LineStage<N, 32, DIR, true, 2>::run(v, buf, t, tw);   // barrier, canonical read, radix 2
+    }
 }
 
 }  // namespace holo
