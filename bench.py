@@ -158,9 +158,9 @@ def subframe_bytes(P, N, L):
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 CSRC = os.path.join(ROOT, "paper_2004_04049_gb300", "csrc")
 KERNEL_SOURCES = {
-    "ospr_col_ifft": ["ospr_kernels.cuh", "fft_core.cuh", "phase_source.cuh", "ospr_col.cu", "tc_dft.cuh"],
-    "ospr_col_fft": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_col.cu", "tc_dft.cuh"],
-    "ospr_row": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_row.cu", "tc_dft.cuh"],
+    "ospr_col_ifft": ["ospr_kernels.cuh", "fft_core.cuh", "phase_source.cuh", "ospr_col.cu"],
+    "ospr_col_fft": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_col.cu"],
+    "ospr_row": ["ospr_kernels.cuh", "fft_core.cuh", "ospr_row.cu"],
     "ospr_finalize": ["ospr.cu"],
 }
 KERNEL_FAMILY = {"k_ospr_col_ifft": "ospr_col_ifft", "k_ospr_col_fft": "ospr_col_fft", "k_ospr_row": "ospr_row",

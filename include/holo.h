@@ -52,8 +52,8 @@ typedef enum holo_status {
 
 typedef enum holo_precision {
     HOLO_FP32 = 0,     /* all transforms in float32 */
-    HOLO_FP16X2 = 1,   /* DFT-32 stages on tensor cores, fp16 hi+lo operands, fp32 accumulate */
-    HOLO_BF16X2 = 2    /* DFT-32 stages on tensor cores, bf16 hi+lo operands, fp32 accumulate */
+    HOLO_FP16X2 = 1,   /* DFT-32 stages on the tcgen05 tensor cores, fp16 hi+lo operands, fp32 accumulate */
+    HOLO_BF16X2 = 2    /* DFT-32 stages on the tcgen05 tensor cores, bf16 hi+lo operands, fp32 accumulate */
 } holo_precision;
 
 /* L value selecting the per-pixel generator with no table (the "unrepeated" case). */
@@ -158,7 +158,10 @@ int ospr_workspace_size(int H, int W, int N, int precision, size_t* bytes);
  *   start_index  draw index of pixel 0 of sub-frame 0 (>= 0): frames that share one
  *                table continue from the previous frame's end (Fig. 3).
  *   subframe_stride  draw-index step between sub-frames; 0 means H*W.
- *   precision    HOLO_FP32 (the tensor-core modes return HOLO_EUNSUPPORTED until built).
+ *   precision    HOLO_FP32, or HOLO_FP16X2 / HOLO_BF16X2: both radix-32 DFT stages of every
+ *                line transform as 64x64 real GEMMs on the tcgen05 tensor cores, operands
+ *                split into hi + lo 16-bit halves, float32 accumulators (far field, H and
+ *                W in {1024, 2048}; HOLO_EUNSUPPORTED otherwise).
  *   d_holo_bits  [N][H*W/32] uint32 output or NULL: bit j of word w is pixel 32*w + j
  *                of that sub-frame, 1 for -1.
  *   d_replay     [H][W] float32 output or NULL: mean replay intensity over sub-frames.
@@ -426,7 +429,7 @@ int gs_workspace_size(int H, int W, int iters, int precision, size_t* bytes);
  *   d_state_in    [H][W][2] float32 (re, im) replay-plane field to resume from, or NULL.
  *   d_state_out   [H][W][2] float32 output or NULL: E after the last iteration.
  *   precision     HOLO_FP32, or HOLO_FP16X2 / HOLO_BF16X2 (the DFT-32 stages of every line
- *                 transform on the tensor cores with split hi/lo operands and float32
+ *                 transform on the tcgen05 tensor cores with split hi/lo operands and float32
  *                 accumulation, as in ospr_generate) for H, W in {1024, 2048}.
  * Errors: HOLO_EINVAL, HOLO_EUNSUPPORTED, HOLO_EWORKSPACE, HOLO_ECUDA.
  */

@@ -135,11 +135,11 @@ __device__ __forceinline__ unsigned* cf_fin(const PFrame& f) { return f.cnt + 4 
 
 template <int NC>
 __device__ __forceinline__ void p_col_ifft(const OsprArgs& a, int tile, int slot) {
-    ospr_col_ifft_body<NC, 0, 0>(a, tile, slot);
+    ospr_col_ifft_body<NC, 0>(a, tile, slot);
 }
 template <int NR>
 __device__ __forceinline__ void p_row(const OsprArgs& a, int row0, int slot) {
-    ospr_row_body<NR, 0, true, 0, false>(a, row0, slot);
+    ospr_row_body<NR, 0, true, false>(a, row0, slot);
 }
 
 // the column DFT tile waits, before each of its pairs, for that pair's row tiles
@@ -149,7 +149,7 @@ __device__ __forceinline__ bool p_col_fft(const PCtl& c, const PFrame& f, const 
     auto before = [&](int j) {
         if (ok) ok = pwait(c, row_done(f) + a.first_pair + j, unsigned(f.row_tiles));
     };
-    ospr_col_fft_body<NC, 0, 0>(a, tile, g, before, NoHook{});
+    ospr_col_fft_body<NC, 0>(a, tile, g, before, NoHook{});
     return ok;
 }
 
@@ -434,7 +434,6 @@ static int persist_frames(const holo_frame_desc* f, int n, PPlan& pl, char* ws, 
         a.bits = d.d_holo_bits;
         a.tw = tab.twiddles;
         a.cs256 = tab.cs256;
-        a.tc = nullptr;
         a.tc05b = nullptr;
         a.fresnel = 0;
         a.chirp_y = a.chirp_x = nullptr;

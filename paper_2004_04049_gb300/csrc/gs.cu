@@ -24,7 +24,7 @@
 #include "fft_core.cuh"
 #include "phase_source.cuh"
 #include "runtime.h"
-#include "tc_dft.cuh"
+#include "tc05_dft.cuh"
 
 namespace holo {
 
@@ -45,10 +45,6 @@ template <> struct GsColCfg<2048, 1> { static constexpr int R = 16, LPC = 4; };
 template <> struct GsColCfg<512, 2>  { static constexpr int R = 16, LPC = 2; };
 template <> struct GsColCfg<1024, 2> { static constexpr int R = 16, LPC = 2; };
 template <> struct GsColCfg<2048, 2> { static constexpr int R = 32, LPC = 2; };
-// tensor-core precisions (variant 3): radix-32 lines, each staged in two buffers
-constexpr int kGsTcVariant = 3;
-template <> struct GsColCfg<1024, 3> { static constexpr int R = 32, LPC = 8; };
-template <> struct GsColCfg<2048, 3> { static constexpr int R = 32, LPC = 4; };
 template <int N, int V> struct GsRowCfg;
 template <> struct GsRowCfg<64, 0>   { static constexpr int R = 2,  LPR = 4; };
 template <> struct GsRowCfg<128, 0>  { static constexpr int R = 4,  LPR = 4; };
@@ -63,8 +59,6 @@ template <> struct GsRowCfg<2048, 1> { static constexpr int R = 16, LPR = 1; };
 template <> struct GsRowCfg<512, 2>  { static constexpr int R = 16, LPR = 2; };
 template <> struct GsRowCfg<1024, 2> { static constexpr int R = 8,  LPR = 2; };
 template <> struct GsRowCfg<2048, 2> { static constexpr int R = 16, LPR = 2; };
-template <> struct GsRowCfg<1024, 3> { static constexpr int R = 32, LPR = 4; };
-template <> struct GsRowCfg<2048, 3> { static constexpr int R = 32, LPR = 2; };
 constexpr bool gs_has_variants(int N) { return N >= 512 && N <= 2048; }
 constexpr int kGsMinLpc = 2;   // the smallest LPC of any variant (bounds the error partials)
 
@@ -93,7 +87,7 @@ struct GsArgs {
     float2* state_out;
     const float2* tw;
     const float2* cs256;
-    const TcFrags* tc;           // DFT-32 A fragments of the tensor-core precision in use
+    const uint8_t* tc05b;        // tcgen05 DFT-32 matrices of the tensor-core precision in use
     float inv_sqrt_p;
     // Fresnel propagation: Q(y, x) = chirp_y[y] * chirp_x[x] (null for the far field)
     const float2* chirp_y;
@@ -102,52 +96,30 @@ struct GsArgs {
 
 template <int NC, int V>
 constexpr int gs_col_stride() { return col_line_stride(NC, GsColCfg<NC, V>::R, GsColCfg<NC, V>::LPC); }
-// the tensor-core precisions (PREC != 0) stage every line in two buffers
-constexpr int gs_nbuf(int prec) { return prec ? 2 : 1; }
 // col_init and row also hold one copy of the cos/sin table (one lookup per pixel)
-template <int NC, int V, int PREC = 0>
+template <int NC, int V>
 constexpr size_t gs_col_smem() {
-    return sizeof(float2) * (256 + size_t(gs_nbuf(PREC)) * GsColCfg<NC, V>::LPC * gs_col_stride<NC, V>());
+    return sizeof(float2) * (256 + size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>());
 }
 // the row pass looks up the quantised codes in a 16-way replicated table (conflict-free)
-template <int NR, int V, int PREC = 0>
+template <int NR, int V>
 constexpr size_t gs_row_smem() {
-    return sizeof(float2) * (kCsSmemEntries + size_t(gs_nbuf(PREC)) * GsRowCfg<NR, V>::LPR *
-                                                  line_stride(NR, GsRowCfg<NR, V>::R));
+    return sizeof(float2) * (kCsSmemEntries + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
 }
 
-// Line FFT of a GS column pass (LPC lines of T threads, lane-consecutive columns); the
-// tensor-core precisions run the DFT-32 stages on mma.sync with split hi/lo operands,
-// warp w working on line w / WPL of the second buffer set.
-template <int NC, int V, int DIR, int PREC>
+// Line FFT of a GS column pass (LPC lines of T threads, lane-consecutive columns)
+template <int NC, int V, int DIR>
 __device__ __forceinline__ void gs_col_line_fft(float2 (&v)[GsColCfg<NC, V>::R], float2* lines, int lc, int t,
                                                 const GsArgs& a) {
-    constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, S = gs_col_stride<NC, V>();
-    if constexpr (PREC == 0) {
-        line_fft<NC, R, DIR, true>(v, lines + lc * S, t, a.tw);
-    } else {
-        static_assert(R == 32 && (NC == 1024 || NC == 2048), "tensor-core stages need radix-32 lines");
-        constexpr int WPL = (NC / R) / 32;
-        float2* lines2 = lines + LPC * S;
-        const int warp = threadIdx.x >> 5;
-        const int wline = warp / WPL, wl = warp % WPL;
-        line_fft_tc<NC, DIR, PREC>(v, lines + lc * S, lines2 + lc * S, lines + wline * S, lines2 + wline * S, t, wl,
-                                   a.tc, a.tw);
-    }
+    constexpr int R = GsColCfg<NC, V>::R, S = gs_col_stride<NC, V>();
+    line_fft<NC, R, DIR, true>(v, lines + lc * S, t, a.tw);
 }
 // Line FFT of the GS row pass: line `line` of LPR, T threads per line
-template <int NR, int V, int DIR, int PREC>
+template <int NR, int V, int DIR>
 __device__ __forceinline__ void gs_row_line_fft(float2 (&v)[GsRowCfg<NR, V>::R], float2* lines, int line, int t,
                                                 const GsArgs& a) {
-    constexpr int R = GsRowCfg<NR, V>::R, LPR = GsRowCfg<NR, V>::LPR, T = NR / R, S = line_stride(NR, R);
-    if constexpr (PREC == 0) {
-        line_fft<NR, R, DIR, (T > 32)>(v, lines + line * S, t, a.tw);
-    } else {
-        static_assert(R == 32 && (NR == 1024 || NR == 2048), "tensor-core stages need radix-32 lines");
-        float2* lines2 = lines + LPR * S;
-        line_fft_tc<NR, DIR, PREC>(v, lines + line * S, lines2 + line * S, lines + line * S, lines2 + line * S, t,
-                                   t >> 5, a.tc, a.tw);
-    }
+    constexpr int R = GsRowCfg<NR, V>::R, T = NR / R, S = line_stride(NR, R);
+    line_fft<NR, R, DIR, (T > 32)>(v, lines + line * S, t, a.tw);
 }
 
 // The arguments of target b of a batch: every per-target buffer advances by b fields;
@@ -189,8 +161,88 @@ __device__ __forceinline__ float gs_scale(const ff* __restrict__ partials, int64
     return tot.hi > 0.f ? sqrtf(ff_div(ff_make(float(P)), tot).hi) : 0.f;
 }
 
+// -------------------------------------------------------- per-pixel steps ----
+// (shared by the float32 passes and the tcgen05 passes of the tensor-core precisions)
+
+// E_0 at rows t + T e of column c: the saved state, or T_s exp(i phi) with phi from the
+// caller or the table draw of target blockIdx.y (looked up in a COPIES-way cos/sin table)
+template <int R, int T, int COPIES>
+__device__ __forceinline__ void gs_initial_field(float2 (&v)[R], const GsArgs& a, const float2* cs, float scale,
+                                                 int t, int c) {
+    const int W = a.W;
+    const SubframeDraw d0 = subframe_draw(a.ps, blockIdx.y);
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const uint32_t p = uint32_t(t + T * e) * uint32_t(W) + uint32_t(c);
+        if (a.state_in) {
+            v[e] = a.state_in[p];
+        } else {
+            const float ts = __ldg(a.target + p) * scale;
+            float2 ph;
+            if (a.init_phase) sincosf(__ldg(a.init_phase + p), &ph.y, &ph.x);
+            else ph = cs_lookup<COPIES>(cs, draw_code(a.ps, d0, p) << a.ps.cs_shift);
+            v[e] = make_float2(ts * ph.x, ts * ph.y);
+        }
+    }
+}
+
+// Row r's IDFT at slots t + T e -> the hologram exp(2 pi i q / levels) with q the phase
+// quantised to the nearest level (codes written when asked). FRESNEL: the field is first
+// multiplied by conj(Q) and the hologram by Q.
+template <int R, int T, bool FRESNEL, int COPIES>
+__device__ __forceinline__ void gs_quantise_row(float2 (&v)[R], const GsArgs& a, const float2* cs, int r, int t) {
+    constexpr int NR = R * T;
+    const int levels = 1 << a.levels_bits;
+    const float k_code = float(levels) * 0.15915494309189533577f;   // levels / (2 pi)
+    const int shift = 8 - a.levels_bits;
+    float2 qy = make_float2(1.f, 0.f);
+    if constexpr (FRESNEL) qy = __ldg(a.chirp_y + r);
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        float2 qc = make_float2(1.f, 0.f);
+        if constexpr (FRESNEL) {
+            qc = cmul(qy, __ldg(a.chirp_x + t + T * e));
+            v[e] = make_float2(fmaf(v[e].x, qc.x, v[e].y * qc.y), fmaf(v[e].y, qc.x, -v[e].x * qc.y));
+        }
+        const float ang = atan2f(v[e].y, v[e].x);
+        const int q = int(floorf(fmaf(ang, k_code, 0.5f))) & (levels - 1);
+        if (a.codes_out) a.codes_out[size_t(r) * NR + t + T * e] = uint8_t(q);
+        v[e] = cs_lookup<COPIES>(cs, uint32_t(q) << shift);
+        if constexpr (FRESNEL) v[e] = cmul(v[e], qc);
+    }
+}
+
+// Amplitude constraint at pixels p0 + e rs of the column DFT: R = DFT / sqrt(P), the
+// error sum of (|R| - T_s)^2 is returned, E = T_s R / |R| (T_s where R = 0) replaces v; the
+// last iteration writes |R|^2 and E instead.
+template <int R, bool LAST>
+__device__ __forceinline__ float gs_constrain(float2 (&v)[R], const float (&tg)[R], const GsArgs& a, float scale,
+                                              size_t p0, size_t rs) {
+    float err = 0.f;
+#pragma unroll
+    for (int e = 0; e < R; ++e) {
+        const size_t p = p0 + e * rs;
+        const float2 Rv = make_float2(v[e].x * a.inv_sqrt_p, v[e].y * a.inv_sqrt_p);
+        const float amp = sqrtf(fmaf(Rv.x, Rv.x, Rv.y * Rv.y));
+        const float ts = tg[e] * scale;
+        const float d = amp - ts;
+        err = fmaf(d, d, err);
+        float2 En = make_float2(ts, 0.f);
+        if (amp > 0.f) {
+            const float f = ts / amp;
+            En = make_float2(Rv.x * f, Rv.y * f);
+        }
+        if constexpr (LAST) {
+            if (a.replay_out) a.replay_out[p] = amp * amp;
+            if (a.state_out) a.state_out[p] = En;
+        }
+        v[e] = En;
+    }
+    return err;
+}
+
 // --------------------------------------------------------------- col_init ----
-template <int NC, int V, int PREC = 0>
+template <int NC, int V>
 __global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC)
 k_gs_col_init(GsArgs a0) {
     constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
@@ -213,23 +265,9 @@ k_gs_col_init(GsArgs a0) {
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     const int c = blockIdx.x * LPC + lc;
-    const float scale = s_scale;
-    const SubframeDraw d0 = subframe_draw(a.ps, blockIdx.y);
     float2 v[R];
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-        const uint32_t p = uint32_t(t + T * e) * uint32_t(W) + uint32_t(c);
-        if (a.state_in) {
-            v[e] = a.state_in[p];
-        } else {
-            const float ts = __ldg(a.target + p) * scale;
-            float2 ph;
-            if (a.init_phase) sincosf(__ldg(a.init_phase + p), &ph.y, &ph.x);
-            else ph = cs_lookup<1>(cs, draw_code(a.ps, d0, p) << a.ps.cs_shift);
-            v[e] = make_float2(ts * ph.x, ts * ph.y);
-        }
-    }
-    gs_col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
+    gs_initial_field<R, T, 1>(v, a, cs, s_scale, t, c);
+    gs_col_line_fft<NC, V, +1>(v, lines, lc, t, a);
     pdl_trigger();
 #pragma unroll
     for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
@@ -237,7 +275,7 @@ k_gs_col_init(GsArgs a0) {
 
 // -------------------------------------------------------------------- row ----
 // FRESNEL: the hologram field is conj(Q) * IDFT(E) and the replay transform takes h * Q.
-template <int NR, int V, bool FRESNEL = false, int PREC = 0>
+template <int NR, int V, bool FRESNEL = false>
 __global__ void __launch_bounds__((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR)
 k_gs_row(GsArgs a0) {
     constexpr int R = GsRowCfg<NR, V>::R, T = NR / R;
@@ -254,36 +292,18 @@ k_gs_row(GsArgs a0) {
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
-    gs_row_line_fft<NR, V, +1, PREC>(v, lines, line, t, a);
-    const int levels = 1 << a.levels_bits;
-    const float k_code = float(levels) * 0.15915494309189533577f;   // levels / (2 pi)
-    const int shift = 8 - a.levels_bits;
-    float2 qy = make_float2(1.f, 0.f);
-    if constexpr (FRESNEL) qy = __ldg(a.chirp_y + r);
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-        float2 qc = make_float2(1.f, 0.f);
-        if constexpr (FRESNEL) {
-            qc = cmul(qy, __ldg(a.chirp_x + t + T * e));
-            v[e] = make_float2(fmaf(v[e].x, qc.x, v[e].y * qc.y), fmaf(v[e].y, qc.x, -v[e].x * qc.y));
-        }
-        const float ang = atan2f(v[e].y, v[e].x);
-        const int q = int(floorf(fmaf(ang, k_code, 0.5f))) & (levels - 1);
-        if (a.codes_out) a.codes_out[size_t(r) * NR + t + T * e] = uint8_t(q);
-        v[e] = cs_lookup(cs, uint32_t(q) << shift);
-        if constexpr (FRESNEL) v[e] = cmul(v[e], qc);
-    }
-    gs_row_line_fft<NR, V, -1, PREC>(v, lines, line, t, a);
+    gs_row_line_fft<NR, V, +1>(v, lines, line, t, a);
+    gs_quantise_row<R, T, FRESNEL, kCsCopies>(v, a, cs, r, t);
+    gs_row_line_fft<NR, V, -1>(v, lines, line, t, a);
     pdl_trigger();
 #pragma unroll
     for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
 }
 
 // -------------------------------------------------------------------- col ----
-// (the tensor-core variant keeps its DFT-32 fragments in registers: one CTA per SM's share)
-template <int NC, int V, bool LAST, int PREC = 0>
+template <int NC, int V, bool LAST>
 __global__ void __launch_bounds__((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC,
-                                  (NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC <= 256 && PREC == 0 ? 2 : 1)
+                                  (NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC <= 256 ? 2 : 1)
 k_gs_col(GsArgs a0) {
     constexpr int R = GsColCfg<NC, V>::R, LPC = GsColCfg<NC, V>::LPC, T = NC / R;
     const GsArgs a = gs_target(a0, blockIdx.y);
@@ -305,34 +325,14 @@ k_gs_col(GsArgs a0) {
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = a.y[p0 + e * rs];
-    gs_col_line_fft<NC, V, -1, PREC>(v, lines, lc, t, a);
-    float err = 0.f;
-#pragma unroll
-    for (int e = 0; e < R; ++e) {
-        const size_t p = p0 + e * rs;
-        const float2 Rv = make_float2(v[e].x * a.inv_sqrt_p, v[e].y * a.inv_sqrt_p);
-        const float amp = sqrtf(fmaf(Rv.x, Rv.x, Rv.y * Rv.y));
-        const float ts = tg[e] * scale;
-        const float d = amp - ts;
-        err = fmaf(d, d, err);
-        float2 En = make_float2(ts, 0.f);
-        if (amp > 0.f) {
-            const float f = ts / amp;
-            En = make_float2(Rv.x * f, Rv.y * f);
-        }
-        if constexpr (LAST) {
-            if (a.replay_out) a.replay_out[p] = amp * amp;
-            if (a.state_out) a.state_out[p] = En;
-        }
-        v[e] = En;
-    }
-    const float errv[1] = {err};
+    gs_col_line_fft<NC, V, -1>(v, lines, lc, t, a);
+    const float errv[1] = {gs_constrain<R, LAST>(v, tg, a, scale, p0, rs)};
     ff b[1];
     block_sums_ff<1>(errv, b, red);
     if (threadIdx.x == 0)
         a.err_part[(size_t(blockIdx.y) * a.iters + size_t(a.iter)) * gridDim.x + blockIdx.x] = b[0];
     if constexpr (!LAST) {
-        gs_col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
+        gs_col_line_fft<NC, V, +1>(v, lines, lc, t, a);
         pdl_trigger();
 #pragma unroll
         for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
@@ -371,25 +371,25 @@ static GsTiles gs_tiles(int H, int W) {
 }
 
 // every launch after k_gs_prepare may overlap the previous kernel's tail (pdl_wait first)
-template <int NC, int V, int PREC = 0>
+template <int NC, int V>
 static int launch_col_init(const GsArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
-    constexpr size_t smem = gs_col_smem<NC, V, PREC>();
-    int rc = ensure_smem((const void*)k_gs_col_init<NC, V, PREC>, smem, &mask);
+    constexpr size_t smem = gs_col_smem<NC, V>();
+    int rc = ensure_smem((const void*)k_gs_col_init<NC, V>, smem, &mask);
     if (rc) return rc;
     Launch ln("gs_col_init", st);
-    const cudaError_t le = launch_pdl(k_gs_col_init<NC, V, PREC>, dim3(a.W / GsColCfg<NC, V>::LPC, a.batch),
+    const cudaError_t le = launch_pdl(k_gs_col_init<NC, V>, dim3(a.W / GsColCfg<NC, V>::LPC, a.batch),
                                       dim3((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC), smem, st, a);
     return ln.done("gs_col_init launch", le);
 }
-template <int NR, int V, bool FRESNEL, int PREC = 0>
+template <int NR, int V, bool FRESNEL>
 static int launch_row_kind(const GsArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
-    constexpr size_t smem = gs_row_smem<NR, V, PREC>();
-    int rc = ensure_smem((const void*)k_gs_row<NR, V, FRESNEL, PREC>, smem, &mask);
+    constexpr size_t smem = gs_row_smem<NR, V>();
+    int rc = ensure_smem((const void*)k_gs_row<NR, V, FRESNEL>, smem, &mask);
     if (rc) return rc;
     Launch ln("gs_row", st);
-    const cudaError_t le = launch_pdl(k_gs_row<NR, V, FRESNEL, PREC>, dim3(a.H / GsRowCfg<NR, V>::LPR, a.batch),
+    const cudaError_t le = launch_pdl(k_gs_row<NR, V, FRESNEL>, dim3(a.H / GsRowCfg<NR, V>::LPR, a.batch),
                                       dim3((NR / GsRowCfg<NR, V>::R) * GsRowCfg<NR, V>::LPR), smem, st, a);
     return ln.done("gs_row launch", le);
 }
@@ -397,21 +397,204 @@ template <int NR, int V>
 static int launch_row(const GsArgs& a, cudaStream_t st) {
     return a.chirp_y ? launch_row_kind<NR, V, true>(a, st) : launch_row_kind<NR, V, false>(a, st);
 }
-template <int NC, int V, int PREC = 0>
+template <int NC, int V>
 static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
     static uint64_t mask0 = 0, mask1 = 0;
-    constexpr size_t smem = sizeof(float2) * size_t(gs_nbuf(PREC)) * GsColCfg<NC, V>::LPC * gs_col_stride<NC, V>();
+    constexpr size_t smem = sizeof(float2) * size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>();
     const dim3 grid(a.W / GsColCfg<NC, V>::LPC, a.batch), threads((NC / GsColCfg<NC, V>::R) * GsColCfg<NC, V>::LPC);
-    int rc = last ? ensure_smem((const void*)k_gs_col<NC, V, true, PREC>, smem, &mask1)
-                  : ensure_smem((const void*)k_gs_col<NC, V, false, PREC>, smem, &mask0);
+    int rc = last ? ensure_smem((const void*)k_gs_col<NC, V, true>, smem, &mask1)
+                  : ensure_smem((const void*)k_gs_col<NC, V, false>, smem, &mask0);
     if (rc) return rc;
     Launch ln("gs_col", st);
-    const cudaError_t le = last ? launch_pdl(k_gs_col<NC, V, true, PREC>, grid, threads, smem, st, a)
-                                : launch_pdl(k_gs_col<NC, V, false, PREC>, grid, threads, smem, st, a);
+    const cudaError_t le = last ? launch_pdl(k_gs_col<NC, V, true>, grid, threads, smem, st, a)
+                                : launch_pdl(k_gs_col<NC, V, false>, grid, threads, smem, st, a);
     return ln.done("gs_col launch", le);
 }
 
-// tensor-core precisions: lengths 1024 and 2048, tile variant 3, far field only
+// ------------------------------------------------- tensor-core precisions ----
+// The three passes with both radix-32 stages of every 1024- or 2048-point line on tcgen05
+// (tc05_dft.cuh: split fp16 / bf16 operands, float32 accumulators in tensor memory), far
+// field only; the per-pixel steps are those of the float32 passes. 256-thread CTAs:
+// 8192 / N columns or rows each. Shared memory from a 1024-byte aligned base: the DFT
+// matrices (hi, lo) of the directions the pass needs, the cos/sin table (col_init: one
+// copy; row: kGsTc05Copies), the padded line buffers (their first 64 KiB also hold the
+// A tiles), two mbarriers.
+static __device__ int g_gs_tc05_fault;
+constexpr int kGsTc05Copies = 4;   // 4-way replicated table: two row CTAs fit on an SM
+
+template <int NC>
+constexpr size_t gs_tc05_col_init_smem() {
+    return 1024 + 2 * kTc05BBytes + sizeof(float2) * 256 + tc05_col_line_bytes<NC>() + 16;
+}
+template <int NR>
+constexpr size_t gs_tc05_row_smem() {
+    return 1024 + 4 * kTc05BBytes + sizeof(float2) * 256 * kGsTc05Copies + tc05_row_line_bytes<NR>() + 16;
+}
+template <int NC>
+constexpr size_t gs_tc05_col_smem() { return 1024 + 4 * kTc05BBytes + tc05_col_line_bytes<NC>() + 16; }
+static_assert((2 * kTc05BBytes + sizeof(float2) * 256) % 1024 == 0 &&
+                  (4 * kTc05BBytes + sizeof(float2) * 256 * kGsTc05Copies) % 1024 == 0,
+              "the line buffers (A tiles) start 1024-byte aligned");
+static_assert(2 * (gs_tc05_row_smem<2048>() + 1024) <= 228 * 1024, "two row CTAs per SM");
+
+template <int NC, int PREC>
+__global__ void __launch_bounds__(kTc05Threads, 1) k_gs_col_init_tc05(GsArgs a0) {
+    constexpr int R = 32, LPC = tc05_lpc<NC>(), T = NC / R, S = tc05_col_stride<NC>();
+    const GsArgs a = gs_target(a0, blockIdx.y);
+    extern __shared__ uint8_t smraw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_scale;
+    uint32_t base;
+    uint8_t* const sm = tc05_smem(smraw, base);
+    float2* cs = reinterpret_cast<float2*>(sm + 2 * kTc05BBytes);
+    float2* lines = cs + 256;
+    const uint32_t lines_u32 = base + 2 * kTc05BBytes + uint32_t(sizeof(float2) * 256);
+    const uint32_t bars = lines_u32 + uint32_t(tc05_col_line_bytes<NC>());
+    tc05_setup(&s_tmem, a.tc05b + 2 * kTc05BBytes, sm, 2, bars);   // direction +1
+    load_cs_table<1>(cs, a.cs256);
+    pdl_wait();
+    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem, &g_gs_tc05_fault);
+    g.b_hi = base;
+    g.b_lo = base + kTc05BBytes;
+    if (threadIdx.x < 32) {
+        const float sc = gs_scale(a.prep_part, int64_t(a.H) * a.W);
+        if (threadIdx.x == 0) {
+            s_scale = sc;
+            if (blockIdx.x == 0) a.sc->scale = sc;
+        }
+    }
+    __syncthreads();
+    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
+    const int W = a.W;
+    const int c = blockIdx.x * LPC + lc;
+    float2 v[R];
+    gs_initial_field<R, T, 1>(v, a, cs, s_scale, t, c);
+    line_fft_tc05<NC, +1, PREC>(v, lines + lc * S, t, a.tw, g);
+    pdl_trigger();
+#pragma unroll
+    for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
+    tc05_teardown(s_tmem);
+}
+
+template <int NR, int PREC>
+__global__ void __launch_bounds__(kTc05Threads, 2) k_gs_row_tc05(GsArgs a0) {
+    constexpr int R = 32, T = NR / R, LPR = tc05_lpc<NR>(), S = line_stride(NR, 32);
+    const GsArgs a = gs_target(a0, blockIdx.y);
+    extern __shared__ uint8_t smraw[];
+    __shared__ uint32_t s_tmem;
+    uint32_t base;
+    uint8_t* const sm = tc05_smem(smraw, base);
+    float2* cs = reinterpret_cast<float2*>(sm + 4 * kTc05BBytes);
+    float2* lines = cs + 256 * kGsTc05Copies;
+    const uint32_t lines_u32 = base + 4 * kTc05BBytes + uint32_t(sizeof(float2) * 256 * kGsTc05Copies);
+    const uint32_t bars = lines_u32 + uint32_t(tc05_row_line_bytes<NR>());
+    tc05_setup(&s_tmem, a.tc05b, sm, 4, bars);   // [-1 hi, -1 lo, +1 hi, +1 lo]
+    load_cs_table<kGsTc05Copies>(cs, a.cs256);
+    pdl_wait();
+    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem, &g_gs_tc05_fault);
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const int r = blockIdx.x * LPR + line;
+    float2* z = a.y + size_t(r) * NR;
+    float2* buf = lines + line * S;
+    float2 v[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
+    g.b_hi = base + 2 * kTc05BBytes;
+    g.b_lo = base + 3 * kTc05BBytes;
+    line_fft_tc05<NR, +1, PREC>(v, buf, t, a.tw, g);
+    gs_quantise_row<R, T, false, kGsTc05Copies>(v, a, cs, r, t);
+    g.b_hi = base;
+    g.b_lo = base + kTc05BBytes;
+    line_fft_tc05<NR, -1, PREC>(v, buf, t, a.tw, g);
+    pdl_trigger();
+#pragma unroll
+    for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
+    tc05_teardown(s_tmem);
+}
+
+template <int NC, bool LAST, int PREC>
+__global__ void __launch_bounds__(kTc05Threads, 1) k_gs_col_tc05(GsArgs a0) {
+    constexpr int R = 32, LPC = tc05_lpc<NC>(), T = NC / R, S = tc05_col_stride<NC>();
+    const GsArgs a = gs_target(a0, blockIdx.y);
+    extern __shared__ uint8_t smraw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ ff red[32];
+    uint32_t base;
+    uint8_t* const sm = tc05_smem(smraw, base);
+    float2* lines = reinterpret_cast<float2*>(sm + 4 * kTc05BBytes);
+    const uint32_t lines_u32 = base + 4 * kTc05BBytes;
+    const uint32_t bars = lines_u32 + uint32_t(tc05_col_line_bytes<NC>());
+    tc05_setup(&s_tmem, a.tc05b, sm, LAST ? 2 : 4, bars);   // [-1 hi, -1 lo (, +1 hi, +1 lo)]
+    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem, &g_gs_tc05_fault);
+    const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
+    const int W = a.W;
+    const int c = blockIdx.x * LPC + lc;
+    pdl_wait();
+    const size_t rs = size_t(T) * W;
+    const size_t p0 = size_t(t) * W + c;
+    float tg[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) tg[e] = __ldg(a.target + p0 + e * rs);
+    const float scale = a.sc->scale;
+    float2 v[R];
+#pragma unroll
+    for (int e = 0; e < R; ++e) v[e] = a.y[p0 + e * rs];
+    g.b_hi = base;
+    g.b_lo = base + kTc05BBytes;
+    line_fft_tc05<NC, -1, PREC>(v, lines + lc * S, t, a.tw, g);
+    const float errv[1] = {gs_constrain<R, LAST>(v, tg, a, scale, p0, rs)};
+    ff b[1];
+    block_sums_ff<1>(errv, b, red);
+    if (threadIdx.x == 0)
+        a.err_part[(size_t(blockIdx.y) * a.iters + size_t(a.iter)) * gridDim.x + blockIdx.x] = b[0];
+    if constexpr (!LAST) {
+        g.b_hi = base + 2 * kTc05BBytes;
+        g.b_lo = base + 3 * kTc05BBytes;
+        line_fft_tc05<NC, +1, PREC>(v, lines + lc * S, t, a.tw, g);
+        pdl_trigger();
+#pragma unroll
+        for (int e = 0; e < R; ++e) a.y[size_t(t + T * e) * W + c] = v[e];
+    }
+    tc05_teardown(s_tmem);
+}
+
+template <int NC, int PREC>
+static int launch_col_init_tc05(const GsArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = gs_tc05_col_init_smem<NC>();
+    int rc = ensure_smem((const void*)k_gs_col_init_tc05<NC, PREC>, smem, &mask);
+    if (rc) return rc;
+    Launch ln("gs_col_init", st);
+    const cudaError_t le = launch_pdl(k_gs_col_init_tc05<NC, PREC>, dim3(a.W / tc05_lpc<NC>(), a.batch),
+                                      dim3(kTc05Threads), smem, st, a);
+    return ln.done("gs_col_init tcgen05 launch", le);
+}
+template <int NR, int PREC>
+static int launch_row_tc05(const GsArgs& a, cudaStream_t st) {
+    static uint64_t mask = 0;
+    constexpr size_t smem = gs_tc05_row_smem<NR>();
+    int rc = ensure_smem((const void*)k_gs_row_tc05<NR, PREC>, smem, &mask);
+    if (rc) return rc;
+    Launch ln("gs_row", st);
+    const cudaError_t le = launch_pdl(k_gs_row_tc05<NR, PREC>, dim3(a.H / tc05_lpc<NR>(), a.batch),
+                                      dim3(kTc05Threads), smem, st, a);
+    return ln.done("gs_row tcgen05 launch", le);
+}
+template <int NC, int PREC>
+static int launch_col_tc05(const GsArgs& a, bool last, cudaStream_t st) {
+    static uint64_t mask0 = 0, mask1 = 0;
+    constexpr size_t smem = gs_tc05_col_smem<NC>();
+    const dim3 grid(a.W / tc05_lpc<NC>(), a.batch);
+    int rc = last ? ensure_smem((const void*)k_gs_col_tc05<NC, true, PREC>, smem, &mask1)
+                  : ensure_smem((const void*)k_gs_col_tc05<NC, false, PREC>, smem, &mask0);
+    if (rc) return rc;
+    Launch ln("gs_col", st);
+    const cudaError_t le = last ? launch_pdl(k_gs_col_tc05<NC, true, PREC>, grid, dim3(kTc05Threads), smem, st, a)
+                                : launch_pdl(k_gs_col_tc05<NC, false, PREC>, grid, dim3(kTc05Threads), smem, st, a);
+    return ln.done("gs_col tcgen05 launch", le);
+}
+
+// tensor-core precisions: lengths 1024 and 2048, far field only
 #define HOLO_GS_TC(n, prec, F)                                                              \
     switch (n) {                                                                            \
         case 1024: return prec == HOLO_BF16X2 ? F(1024, kTcBf16) : F(1024, kTcFp16);        \
@@ -419,17 +602,17 @@ static int launch_col(const GsArgs& a, bool last, cudaStream_t st) {
         default: return fail(HOLO_EUNSUPPORTED, "tensor-core GS: line length %d", n);     \
     }
 static int run_col_init_tc(const GsArgs& a, int prec, cudaStream_t st) {
-#define C(n, p) launch_col_init<n, kGsTcVariant, p>(a, st)
+#define C(n, p) launch_col_init_tc05<n, p>(a, st)
     HOLO_GS_TC(a.H, prec, C)
 #undef C
 }
 static int run_row_tc(const GsArgs& a, int prec, cudaStream_t st) {
-#define C(n, p) launch_row_kind<n, kGsTcVariant, false, p>(a, st)
+#define C(n, p) launch_row_tc05<n, p>(a, st)
     HOLO_GS_TC(a.W, prec, C)
 #undef C
 }
 static int run_col_tc(const GsArgs& a, int prec, bool last, cudaStream_t st) {
-#define C(n, p) launch_col<n, kGsTcVariant, p>(a, last, st)
+#define C(n, p) launch_col_tc05<n, p>(a, last, st)
     HOLO_GS_TC(a.H, prec, C)
 #undef C
 }
@@ -567,7 +750,7 @@ static int gs_iterate_impl(const char* who, int B, const float* d_target, int H,
     a.state_out = reinterpret_cast<float2*>(d_state_out);
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
-    a.tc = tab.tc[precision];
+    a.tc05b = tab.tc05b[precision];
     a.inv_sqrt_p = float(1.0 / std::sqrt(double(H) * double(W)));
     a.chirp_y = a.chirp_x = nullptr;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
@@ -597,7 +780,7 @@ static int gs_iterate_impl(const char* who, int B, const float* d_target, int H,
         if ((rc = tc ? run_col_tc(a, precision, last, st) : run_col(a, tiles.col_v, last, st))) return rc;
     }
     if (d_err) {
-        const int nb = tc ? W / (H == 1024 ? GsColCfg<1024, kGsTcVariant>::LPC : GsColCfg<2048, kGsTcVariant>::LPC)
+        const int nb = tc ? W / (H == 1024 ? tc05_lpc<1024>() : tc05_lpc<2048>())
                           : col_blocks(H, W, tiles.col_v);
         if (nb < 1) return HOLO_EUNSUPPORTED;
         Launch ln("gs_finish", st);
@@ -665,6 +848,19 @@ extern "C" int gs_iterate_fresnel(const float* d_target, int H, int W, int iters
 }
 
 namespace holo {
+
+int gs_tc05_fault(int* out, bool clear) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_gs_tc05_fault, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e, "gs_tc05_fault");
+    if (clear && v) {
+        const int z = 0;
+        if ((e = cudaMemcpyToSymbol(g_gs_tc05_fault, &z, sizeof(int))) != cudaSuccess)
+            return cuda_status(e, "gs_tc05_fault");
+    }
+    *out = v;
+    return HOLO_OK;
+}
 
 // phase[p] = arg(state[p]) in (-pi, pi], with arg(0) = 0 whatever the zeros' signs
 __global__ void k_gs_state_phase(const float2* __restrict__ state, int64_t n, float* __restrict__ phase) {

@@ -316,7 +316,6 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.bits = d_holo_bits;
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
-    a.tc = tab.tc[precision];
     a.tc05b = tab.tc05b[precision];
     a.fresnel = 0;
     a.chirp_y = a.chirp_x = nullptr;
@@ -387,7 +386,6 @@ extern "C" int ospr_generate_fresnel(const float* d_target, int H, int W, int N,
     a.bits = d_holo_bits;
     a.tw = tab.twiddles;
     a.cs256 = tab.cs256;
-    a.tc = nullptr;
     a.tc05b = nullptr;
     a.fresnel = 1;
     a.chirp_y = chirp;
@@ -617,7 +615,6 @@ extern "C" int ospr_generate_noalloc(const float* d_target, int H, int W, int N,
     a.W = W;
     a.N = N;
     a.ps = ps;
-    a.tc = nullptr;
     a.tc05b = nullptr;
     a.zbuf = static_cast<float2*>(scratch);
     a.sacc = reinterpret_cast<float*>(static_cast<char*>(scratch) + pl.z_bytes);

@@ -8,11 +8,11 @@ template <int NC, int V>
 static int launch_col_ifft(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
     constexpr size_t smem = col_ifft_smem_bytes<NC, V>();
-    int rc = ensure_smem((const void*)k_ospr_col_ifft<NC, V, 0>, smem, &mask);
+    int rc = ensure_smem((const void*)k_ospr_col_ifft<NC, V>, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC, V>::LPC, a.pairs);
     Launch ln("ospr_col_ifft", st);
-    const cudaError_t le = launch_pdl(k_ospr_col_ifft<NC, V, 0>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
+    const cudaError_t le = launch_pdl(k_ospr_col_ifft<NC, V>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
     return ln.done("ospr_col_ifft launch", le);
 }
 
@@ -20,11 +20,11 @@ template <int NC, int V>
 static int launch_col_fft(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
     constexpr size_t smem = col_fft_smem_bytes<NC, V>();
-    int rc = ensure_smem((const void*)k_ospr_col_fft<NC, V, 0>, smem, &mask);
+    int rc = ensure_smem((const void*)k_ospr_col_fft<NC, V>, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.W / ColCfg<NC, V>::LPC, a.groups);
     Launch ln("ospr_col_fft", st);
-    const cudaError_t le = launch_pdl(k_ospr_col_fft<NC, V, 0>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
+    const cudaError_t le = launch_pdl(k_ospr_col_fft<NC, V>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
     return ln.done("ospr_col_fft launch", le);
 }
 

@@ -25,7 +25,6 @@
 #include "fft_core.cuh"
 #include "phase_source.cuh"
 #include "runtime.h"
-#include "tc_dft.cuh"
 
 namespace holo {
 
@@ -80,7 +79,6 @@ struct OsprArgs {
     int accumulate;       // add to sacc instead of overwriting
     const float2* tw;
     const float2* cs256;
-    const TcFrags* tc;    // DFT-32 A fragments of the tensor-core precision in use
     const uint8_t* tc05b; // tcgen05 DFT-32 matrices of that precision ([direction][hi, lo])
     // Fresnel propagation: one sub-frame per field slot (no two-for-one packing) and the
     // quadratic phase Q(y, x) = chirp_y[y] * chirp_x[x]; 0 / null for the far field
@@ -98,55 +96,35 @@ __device__ __forceinline__ int slot_subframe(const OsprArgs& a, int slot, bool& 
 
 template <int NC, int V>
 constexpr int col_stride() { return col_line_stride(NC, ColCfg<NC, V>::R, ColCfg<NC, V>::LPC); }
-// tensor-core precisions stage every line in two buffers (PREC != 0)
-constexpr int nbuf(int prec) { return prec ? 2 : 1; }
 // pass 1 also holds the replicated cos/sin table
-template <int NC, int V, int PREC = 0>
+template <int NC, int V>
 constexpr size_t col_ifft_smem_bytes() {
-    return sizeof(float2) * (kCsSmemEntries + size_t(nbuf(PREC)) * ColCfg<NC, V>::LPC * col_stride<NC, V>());
+    return sizeof(float2) * (kCsSmemEntries + size_t(ColCfg<NC, V>::LPC) * col_stride<NC, V>());
 }
-template <int NC, int V, int PREC = 0>
+template <int NC, int V>
 constexpr size_t col_fft_smem_bytes() {
-    return sizeof(float2) * size_t(nbuf(PREC)) * ColCfg<NC, V>::LPC * col_stride<NC, V>();
+    return sizeof(float2) * size_t(ColCfg<NC, V>::LPC) * col_stride<NC, V>();
 }
-template <int NR, int V, int PREC = 0>
+template <int NR, int V>
 constexpr size_t row_smem_bytes() {
-    return sizeof(float2) * size_t(nbuf(PREC)) * RowCfg<NR, V>::LPR * line_stride(NR, RowCfg<NR, V>::R);
+    return sizeof(float2) * size_t(RowCfg<NR, V>::LPR) * line_stride(NR, RowCfg<NR, V>::R);
 }
 
-// Line FFT of a column pass: `lines` holds LPC line buffers (and LPC more for the
-// tensor-core precisions, whose warps each work on one line: warp w on line w / WPL).
-template <int NC, int V, int DIR, int PREC>
+// Line FFT of a column pass: line lc of the LPC line buffers at `lines`
+template <int NC, int V, int DIR>
 __device__ __forceinline__ void col_line_fft(float2 (&v)[ColCfg<NC, V>::R], float2* lines, int lc, int t,
                                              const OsprArgs& a) {
-    constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, S = col_stride<NC, V>();
-    if constexpr (PREC == 0) {
-        line_fft<NC, R, DIR, true>(v, lines + lc * S, t, a.tw);
-    } else {
-        static_assert(R == 32 && (NC == 1024 || NC == 2048), "tensor-core stages need radix-32 lines");
-        constexpr int WPL = (NC / R) / 32;
-        float2* lines2 = lines + LPC * S;
-        const int warp = threadIdx.x >> 5;
-        const int wline = warp / WPL, wl = warp % WPL;
-        line_fft_tc<NC, DIR, PREC>(v, lines + lc * S, lines2 + lc * S, lines + wline * S, lines2 + wline * S, t, wl,
-                                   a.tc, a.tw);
-    }
+    constexpr int R = ColCfg<NC, V>::R, S = col_stride<NC, V>();
+    line_fft<NC, R, DIR, true>(v, lines + lc * S, t, a.tw);
 }
 
 // Line FFT of a row pass: line `line` of LPR, T = N/R threads per line.
-template <int NR, int V, int DIR, int PREC>
+template <int NR, int V, int DIR>
 __device__ __forceinline__ void row_line_fft(float2 (&v)[RowCfg<NR, V>::R], float2* lines, int line, int t,
                                              const OsprArgs& a) {
-    constexpr int R = RowCfg<NR, V>::R, LPR = RowCfg<NR, V>::LPR, T = NR / R;
+    constexpr int R = RowCfg<NR, V>::R, T = NR / R;
     constexpr int S = line_stride(NR, R);
-    if constexpr (PREC == 0) {
-        line_fft<NR, R, DIR, (T > 32)>(v, lines + line * S, t, a.tw);
-    } else {
-        static_assert(R == 32 && (NR == 1024 || NR == 2048), "tensor-core stages need radix-32 lines");
-        float2* lines2 = lines + LPR * S;
-        line_fft_tc<NR, DIR, PREC>(v, lines + line * S, lines2 + line * S, lines + line * S, lines2 + line * S, t,
-                                   t >> 5, a.tc, a.tw);
-    }
+    line_fft<NR, R, DIR, (T > 32)>(v, lines + line * S, t, a.tw);
 }
 
 // ------------------------------------------------------------------ pass 1 ----
@@ -298,7 +276,7 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
 
 // Pass 1 on column tile `tile` (LPC/2 mirror column pairs) of field slot `slot`; every
 // thread of the CTA (ColCfg threads) calls it.
-template <int NC, int V, int PREC>
+template <int NC, int V>
 __device__ __forceinline__ void ospr_col_ifft_body(const OsprArgs& a, int tile, int slot) {
     constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R, S = col_stride<NC, V>();
     static_assert(stage_count(NC, R) > 1, "the line FFT's opening barrier guards the exchange buffer");
@@ -334,17 +312,17 @@ __device__ __forceinline__ void ospr_col_ifft_body(const OsprArgs& a, int tile, 
         for (int e = R / 2; e < R; ++e)
             if (t > 0 || e > R / 2) v[e] = own[pad_index<R>(t + T * e)];
     }
-    col_line_fft<NC, V, +1, PREC>(v, lines, lc, t, a);
+    col_line_fft<NC, V, +1>(v, lines, lc, t, a);
     pdl_trigger();
     float2* z = a.zbuf + size_t(slot) * size_t(NC) * size_t(W);
 #pragma unroll
     for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
 }
 
-template <int NC, int V, int PREC>
+template <int NC, int V>
 __global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
 k_ospr_col_ifft(OsprArgs a) {
-    ospr_col_ifft_body<NC, V, PREC>(a, int(blockIdx.x), int(blockIdx.y));
+    ospr_col_ifft_body<NC, V>(a, int(blockIdx.x), int(blockIdx.y));
 }
 
 // ------------------------------------------------------------------ pass 2 ----
@@ -352,7 +330,7 @@ k_ospr_col_ifft(OsprArgs a) {
 // binarised on its real part, and the replay transform takes h * Q.
 // Rows row0 + threadIdx.x / T of field slot `slot` (a CTA of any multiple of T threads
 // holds that many lines; the kernel below uses RowCfg's LPR lines per CTA).
-template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL>
+template <int NR, int V, bool REPLAY, bool FRESNEL>
 __device__ __forceinline__ void ospr_row_body(const OsprArgs& a, int row0, int slot) {
     constexpr int R = RowCfg<NR, V>::R, T = NR / R;
     extern __shared__ float2 sm[];
@@ -367,7 +345,7 @@ __device__ __forceinline__ void ospr_row_body(const OsprArgs& a, int row0, int s
     float2 v[R];
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
-    row_line_fft<NR, V, +1, PREC>(v, sm, line, t, a);
+    row_line_fft<NR, V, +1>(v, sm, line, t, a);
 
     float2 qy = make_float2(1.f, 0.f);
     if constexpr (FRESNEL) qy = __ldg(a.chirp_y + r);
@@ -394,17 +372,17 @@ __device__ __forceinline__ void ospr_row_body(const OsprArgs& a, int row0, int s
         else v[e] = make_float2(n0 ? -1.f : 1.f, single ? 0.f : (n1 ? -1.f : 1.f));
     }
     if constexpr (REPLAY) {
-        row_line_fft<NR, V, -1, PREC>(v, sm, line, t, a);
+        row_line_fft<NR, V, -1>(v, sm, line, t, a);
         pdl_trigger();
 #pragma unroll
         for (int e = 0; e < R; ++e) z[t + T * e] = v[e];
     }
 }
 
-template <int NR, int V, bool REPLAY, int PREC, bool FRESNEL = false>
+template <int NR, int V, bool REPLAY, bool FRESNEL = false>
 __global__ void __launch_bounds__((NR / RowCfg<NR, V>::R) * RowCfg<NR, V>::LPR)
 k_ospr_row(OsprArgs a) {
-    ospr_row_body<NR, V, REPLAY, PREC, FRESNEL>(a, int(blockIdx.x) * RowCfg<NR, V>::LPR, int(blockIdx.y));
+    ospr_row_body<NR, V, REPLAY, FRESNEL>(a, int(blockIdx.x) * RowCfg<NR, V>::LPR, int(blockIdx.y));
 }
 
 
@@ -416,7 +394,7 @@ k_ospr_row(OsprArgs a) {
 struct NoHook {
     __device__ __forceinline__ void operator()(int) const {}
 };
-template <int NC, int V, int PREC, class Before = NoHook, class After = NoHook>
+template <int NC, int V, class Before = NoHook, class After = NoHook>
 __device__ __forceinline__ void ospr_col_fft_body(const OsprArgs& a, int tile, int g, Before before_pair = {},
                                                   After after_read = {}) {
     constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R;
@@ -437,7 +415,7 @@ __device__ __forceinline__ void ospr_col_fft_body(const OsprArgs& a, int tile, i
 #pragma unroll
         for (int e = 0; e < R; ++e) v[e] = z[size_t(t + T * e) * W + c];
         after_read(j);
-        col_line_fft<NC, V, -1, PREC>(v, lines, lc, t, a);
+        col_line_fft<NC, V, -1>(v, lines, lc, t, a);
 #pragma unroll
         for (int e = 0; e < R; ++e) acc[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, acc[e]));
     }
@@ -450,10 +428,10 @@ __device__ __forceinline__ void ospr_col_fft_body(const OsprArgs& a, int tile, i
     }
 }
 
-template <int NC, int V, int PREC>
+template <int NC, int V>
 __global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
 k_ospr_col_fft(OsprArgs a) {
-    ospr_col_fft_body<NC, V, PREC>(a, int(blockIdx.x), int(blockIdx.y));
+    ospr_col_fft_body<NC, V>(a, int(blockIdx.x), int(blockIdx.y));
 }
 
 

@@ -8,7 +8,7 @@ template <int NR, int V, bool REPLAY, bool FRESNEL>
 static int launch_row(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
     constexpr size_t smem = row_smem_bytes<NR, V>();
-    void (*kern)(OsprArgs) = k_ospr_row<NR, V, REPLAY, 0, FRESNEL>;
+    void (*kern)(OsprArgs) = k_ospr_row<NR, V, REPLAY, FRESNEL>;
     int rc = ensure_smem((const void*)kern, smem, &mask);
     if (rc) return rc;
     dim3 grid(a.H / RowCfg<NR, V>::LPR, a.pairs);

@@ -2,11 +2,9 @@
 // cores (tcgen05.mma: split fp16 or bf16 operands, float32 accumulators in tensor memory;
 // tc05_dft.cuh), for line lengths 1024 and 2048.
 //
-// Every pass runs 256-thread CTAs, two MMA groups of 128 sub-lines: a column pass holds
-// LPC = 8192 / NC columns of NC/32 threads, a row pass 8192 / NR rows. Shared memory, from
-// a 1024-byte aligned base: the DFT matrices (hi, lo) of the directions the pass needs,
-// the replicated cos/sin table (build pass only), the padded line buffers, whose first
-// 64 KiB also hold the groups' A tiles, and two mbarriers.
+// Shared memory of a pass, from a 1024-byte aligned base: the DFT matrices (hi, lo) of the
+// directions the pass needs, the replicated cos/sin table (build pass only), the padded
+// line buffers, whose first 64 KiB also hold the groups' A tiles, and two mbarriers.
 #include "ospr_kernels.cuh"
 #include "tc05_dft.cuh"
 
@@ -14,15 +12,6 @@ namespace holo {
 
 static __device__ int g_tc05_dft_fault;
 
-constexpr int kTc05Threads = 256;
-template <int N>
-constexpr int tc05_lpc() { return kTc05Threads / (N / 32); }
-template <int N>
-constexpr int tc05_col_stride() { return col_line_stride(N, 32, tc05_lpc<N>()); }
-template <int N>
-constexpr size_t tc05_col_line_bytes() { return sizeof(float2) * tc05_lpc<N>() * tc05_col_stride<N>(); }
-template <int N>
-constexpr size_t tc05_row_line_bytes() { return sizeof(float2) * tc05_lpc<N>() * line_stride(N, 32); }
 template <int N>
 constexpr size_t tc05_col_fft_smem() { return 1024 + 2 * kTc05BBytes + tc05_col_line_bytes<N>() + 16; }
 template <int N>
@@ -34,64 +23,7 @@ constexpr size_t tc05_row_smem() { return 1024 + 4 * kTc05BBytes + tc05_row_line
 static_assert(tc05_lpc<1024>() == ColCfg<1024, 1>::LPC && tc05_lpc<2048>() == ColCfg<2048, 1>::LPC &&
                   ColCfg<1024, 1>::R == 32 && ColCfg<2048, 1>::R == 32,
               "the build pass uses the radix-32 column tiles of variant 1");
-static_assert(tc05_col_line_bytes<1024>() >= 4 * kTc05TileBytes && tc05_col_line_bytes<2048>() >= 4 * kTc05TileBytes &&
-                  tc05_row_line_bytes<1024>() >= 4 * kTc05TileBytes && tc05_row_line_bytes<2048>() >= 4 * kTc05TileBytes,
-              "the A tiles of both groups fit in the line buffers");
 static_assert(tc05_col_ifft_smem<2048>() <= 227 * 1024 && tc05_row_smem<2048>() <= 227 * 1024, "shared memory");
-
-// TMEM (128 columns), the B tiles and the mbarriers of a pass, set up by every thread of
-// the CTA: `nb` B tiles are copied from `bsrc` to the start of shared memory `bdst`, the
-// two mbarriers (one per MMA group) sit at shared address `bars`.
-__device__ __forceinline__ void tc05_setup(uint32_t* s_tmem, const uint8_t* bsrc, uint8_t* bdst, int nb,
-                                           uint32_t bars) {
-    const int tid = threadIdx.x;
-    if ((tid >> 5) == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(
-                         static_cast<uint32_t>(__cvta_generic_to_shared(s_tmem)))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bars) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bars + 8) : "memory");
-    }
-    const uint4* src = reinterpret_cast<const uint4*>(bsrc);
-    uint4* dst = reinterpret_cast<uint4*>(bdst);
-    for (int i = tid; i < nb * kTc05BBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-}
-// after tc05_setup and any other shared-memory fill: the CTA barrier that publishes them
-// (the TMEM address that warp 0's allocation wrote included: it is read after the
-// barrier), then the MMA group of this thread (A tiles at `atiles`, 2 x kTc05TileBytes
-// per group)
-__device__ __forceinline__ Tc05Group tc05_group(uint32_t atiles, uint32_t bars, const uint32_t* s_tmem) {
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem_addr = *reinterpret_cast<const volatile uint32_t*>(s_tmem);
-    Tc05Group g;
-    const int grp = threadIdx.x >> 7;
-    g.row = threadIdx.x & 127;
-    g.a_hi = atiles + uint32_t(grp) * 2u * kTc05TileBytes;
-    g.a_lo = g.a_hi + kTc05TileBytes;
-    g.b_hi = g.b_lo = 0;
-    g.bar = bars + 8u * grp;
-    g.tmem = tmem_addr + 64u * grp;
-    g.phase = 0;
-    g.fault = &g_tc05_dft_fault;
-    return g;
-}
-__device__ __forceinline__ void tc05_teardown(uint32_t tmem_addr) {
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem_addr) : "memory");
-}
-// the 1024-byte aligned start of the dynamic shared memory (generic and shared address)
-__device__ __forceinline__ uint8_t* tc05_smem(uint8_t* smraw, uint32_t& base) {
-    const uint32_t raw = static_cast<uint32_t>(__cvta_generic_to_shared(smraw));
-    base = (raw + 1023u) & ~1023u;
-    return smraw + (base - raw);
-}
 
 // Build + column IDFT pass (k_ospr_col_ifft): mirror column pairs as in the float32 pass,
 // both radix-32 stages on tcgen05 with the inverse-direction matrix.
@@ -110,7 +42,7 @@ __global__ void __launch_bounds__(kTc05Threads, 1) k_ospr_col_ifft_tc05(OsprArgs
     tc05_setup(&s_tmem, a.tc05b + 2 * kTc05BBytes, sm, 2, bars);
     load_cs_table(cs, a.cs256);
     pdl_wait();   // the table and target may be written by the previous kernel
-    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem);
+    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem, &g_tc05_dft_fault);
     g.b_hi = base;
     g.b_lo = base + kTc05BBytes;
 
@@ -162,7 +94,7 @@ __global__ void __launch_bounds__(kTc05Threads, 2) k_ospr_row_tc05(OsprArgs a) {
     const uint32_t lines_u32 = base + 4 * kTc05BBytes;
     const uint32_t bars = lines_u32 + uint32_t(tc05_row_line_bytes<NR>());
     tc05_setup(&s_tmem, a.tc05b, sm, 4, bars);   // [-1 hi, -1 lo, +1 hi, +1 lo]
-    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem);
+    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem, &g_tc05_dft_fault);
 
     const int tid = threadIdx.x;
     const int line = tid / T, t = tid % T;
@@ -220,7 +152,7 @@ __global__ void __launch_bounds__(kTc05Threads, 2) k_ospr_col_fft_tc05(OsprArgs 
     const uint32_t lines_u32 = base + 2 * kTc05BBytes;
     const uint32_t bars = lines_u32 + uint32_t(tc05_col_line_bytes<NC>());
     tc05_setup(&s_tmem, a.tc05b, sm, 2, bars);   // direction -1: the first pair
-    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem);
+    Tc05Group g = tc05_group(lines_u32, bars, &s_tmem, &g_tc05_dft_fault);
     g.b_hi = base;
     g.b_lo = base + kTc05BBytes;
 

@@ -14,7 +14,6 @@
 
 #include "fft_core.cuh"
 #include "tc05_dft.cuh"
-#include "tc_dft.cuh"
 
 namespace holo {
 
@@ -142,46 +141,6 @@ static int collect_locked() {
 // ---------------------------------------------------------- device tables ----
 static __device__ float2 g_twiddles[kTwiddleTotal];
 static __device__ float2 g_cs256[256];
-static __device__ TcFrags g_tc_frags[2];   // fp16, bf16
-
-// A fragments (hi and lo) of the 32x32 cos and sin matrices in the mma.m16n8k16 layout
-static void host_tc_frags(TcFrags* out, bool bf16) {
-    const double two_pi = 6.283185307179586476925286766559;
-    auto conv = [&](float x) -> uint16_t {
-        if (bf16) {
-            const __nv_bfloat16 b = __float2bfloat16_rn(x);
-            return *reinterpret_cast<const uint16_t*>(&b);
-        }
-        const __half h = __float2half_rn(x);
-        return *reinterpret_cast<const uint16_t*>(&h);
-    };
-    auto back = [&](uint16_t u) -> float {
-        if (bf16) return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(&u));
-        return __half2float(*reinterpret_cast<const __half*>(&u));
-    };
-    for (int mat = 0; mat < 2; ++mat)
-        for (int tile = 0; tile < 4; ++tile)
-            for (int lane = 0; lane < 32; ++lane) {
-                const int mt = tile >> 1, kt = tile & 1, g = lane >> 2, cc = lane & 3;
-                const int rows[4] = {16 * mt + g, 16 * mt + g + 8, 16 * mt + g, 16 * mt + g + 8};
-                const int cols[4] = {16 * kt + 2 * cc, 16 * kt + 2 * cc, 16 * kt + 2 * cc + 8, 16 * kt + 2 * cc + 8};
-                for (int reg = 0; reg < 4; ++reg) {
-                    uint32_t hi = 0, lo = 0;
-                    for (int half = 0; half < 2; ++half) {
-                        const int k = rows[reg], m = cols[reg] + half;
-                        const double ang = two_pi * double(k) * double(m) / 32.0;
-                        const float x = float(mat == 0 ? std::cos(ang) : std::sin(ang));
-                        const uint16_t h = conv(x);
-                        const uint16_t l = conv(x - back(h));
-                        hi |= uint32_t(h) << (16 * half);
-                        lo |= uint32_t(l) << (16 * half);
-                    }
-                    out->v[mat][0][tile][lane][reg] = hi;
-                    out->v[mat][1][tile][lane][reg] = lo;
-                }
-            }
-}
-
 // tcgen05 DFT-32 B operands: [precision fp16, bf16][direction -1, +1][hi, lo][8192 bytes].
 // Row j (output) holds the coefficients of input i (K): outputs 0..31 are Re X_k, 32..63
 // Im X_k; inputs 0..31 are Re x_n, 32..63 Im x_n; X_k = sum_n x_n exp(i DIR 2 pi n k / 32).
@@ -264,11 +223,6 @@ int device_tables(Tables* out) {
         if (e != cudaSuccess) return cuda_status(e, "upload twiddles");
         e = cudaMemcpyToSymbol(g_cs256, cs.data(), sizeof(float2) * 256);
         if (e != cudaSuccess) return cuda_status(e, "upload cos/sin table");
-        std::vector<TcFrags> fr(2);
-        host_tc_frags(&fr[0], false);
-        host_tc_frags(&fr[1], true);
-        e = cudaMemcpyToSymbol(g_tc_frags, fr.data(), sizeof(TcFrags) * 2);
-        if (e != cudaSuccess) return cuda_status(e, "upload tensor-core fragments");
         std::vector<uint8_t> b05(sizeof(g_tc05_b));
         host_tc05_b(b05.data(), false);
         host_tc05_b(b05.data() + b05.size() / 2, true);
@@ -281,11 +235,6 @@ int device_tables(Tables* out) {
         e = cudaGetSymbolAddress(&p, g_cs256);
         if (e != cudaSuccess) return cuda_status(e, "cos/sin table address");
         g_tables[dev].cs256 = static_cast<const float2*>(p);
-        e = cudaGetSymbolAddress(&p, g_tc_frags);
-        if (e != cudaSuccess) return cuda_status(e, "tensor-core fragment address");
-        g_tables[dev].tc[0] = nullptr;
-        g_tables[dev].tc[1] = static_cast<const TcFrags*>(p);
-        g_tables[dev].tc[2] = static_cast<const TcFrags*>(p) + 1;
         e = cudaGetSymbolAddress(&p, g_tc05_b);
         if (e != cudaSuccess) return cuda_status(e, "tcgen05 DFT matrix address");
         g_tables[dev].tc05b[0] = nullptr;

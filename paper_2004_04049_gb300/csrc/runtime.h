@@ -76,11 +76,9 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 }
 
 // ---- constant tables ---------------------------------------------------------
-struct TcFrags;
 struct Tables {
     const float2* twiddles;   // Stockham stage twiddles, see fft_core.cuh
     const float2* cs256;      // (cos, sin)(2*pi*c/256), c < 256
-    const TcFrags* tc[3];     // DFT-32 A fragments per tensor-core precision (index 1 fp16, 2 bf16)
     // tcgen05 DFT-32 B operand per precision (index 1 fp16, 2 bf16): [direction -1, +1][hi, lo]
     // 64x64 real-form matrices, 8192 bytes each in the K-major 128-byte-swizzle layout
     const uint8_t* tc05b[3];

@@ -22,6 +22,9 @@
 
 namespace holo {
 
+// the tensor-core precisions (holo.h HOLO_FP16X2, HOLO_BF16X2)
+enum TcPrec : int { kTcFp16 = 1, kTcBf16 = 2 };
+
 constexpr int kTc05TileBytes = 128 * 128;   // A tile: 128 rows x 128 bytes
 constexpr int kTc05BBytes = 64 * 128;       // B tile: 64 rows x 128 bytes
 constexpr uint32_t kTc05WaitLimit = 1u << 22;
@@ -203,6 +206,77 @@ __device__ __forceinline__ void line_fft_tc05(float2 (&v)[32], float2* buf, int 
         for (int m = 0; m < 32; ++m) buf[pad_index<32>((t >> 5) * 1024 + k + 32 * m)] = v[m];
         LineStage<N, 32, DIR, true, 2>::run(v, buf, t, tw);   // barrier, canonical read, radix 2
     }
+}
+
+// ------------------------------------------------- kernel setup of a pass ----
+// A pass on tcgen05 runs 256-thread CTAs, two MMA groups of 128 sub-lines: a column pass
+// holds 8192 / N columns of N/32 threads, a row pass 8192 / N rows. The A tiles of both
+// groups (64 KiB) share memory with the padded line buffers.
+constexpr int kTc05Threads = 256;
+template <int N>
+constexpr int tc05_lpc() { return kTc05Threads / (N / 32); }
+template <int N>
+constexpr int tc05_col_stride() { return col_line_stride(N, 32, tc05_lpc<N>()); }
+template <int N>
+constexpr size_t tc05_col_line_bytes() { return sizeof(float2) * tc05_lpc<N>() * tc05_col_stride<N>(); }
+template <int N>
+constexpr size_t tc05_row_line_bytes() { return sizeof(float2) * tc05_lpc<N>() * line_stride(N, 32); }
+static_assert(tc05_col_line_bytes<1024>() >= 4 * kTc05TileBytes && tc05_col_line_bytes<2048>() >= 4 * kTc05TileBytes &&
+                  tc05_row_line_bytes<1024>() >= 4 * kTc05TileBytes && tc05_row_line_bytes<2048>() >= 4 * kTc05TileBytes,
+              "the A tiles of both groups fit in the line buffers");
+
+// TMEM (128 columns), the B tiles and the mbarriers of a pass, set up by every thread of
+// the CTA: `nb` B tiles are copied from `bsrc` to the start of shared memory `bdst`, the
+// two mbarriers (one per MMA group) sit at shared address `bars`.
+__device__ __forceinline__ void tc05_setup(uint32_t* s_tmem, const uint8_t* bsrc, uint8_t* bdst, int nb,
+                                           uint32_t bars) {
+    const int tid = threadIdx.x;
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(s_tmem)))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bars) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bars + 8) : "memory");
+    }
+    const uint4* src = reinterpret_cast<const uint4*>(bsrc);
+    uint4* dst = reinterpret_cast<uint4*>(bdst);
+    for (int i = tid; i < nb * kTc05BBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+// after tc05_setup and any other shared-memory fill: the CTA barrier that publishes them
+// (the TMEM address that warp 0's allocation wrote included: it is read after the
+// barrier), then the MMA group of this thread (A tiles at `atiles`, 2 x kTc05TileBytes
+// per group; an expired wait sets *fault)
+__device__ __forceinline__ Tc05Group tc05_group(uint32_t atiles, uint32_t bars, const uint32_t* s_tmem, int* fault) {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem_addr = *reinterpret_cast<const volatile uint32_t*>(s_tmem);
+    Tc05Group g;
+    const int grp = threadIdx.x >> 7;
+    g.row = threadIdx.x & 127;
+    g.a_hi = atiles + uint32_t(grp) * 2u * kTc05TileBytes;
+    g.a_lo = g.a_hi + kTc05TileBytes;
+    g.b_hi = g.b_lo = 0;
+    g.bar = bars + 8u * grp;
+    g.tmem = tmem_addr + 64u * grp;
+    g.phase = 0;
+    g.fault = fault;
+    return g;
+}
+__device__ __forceinline__ void tc05_teardown(uint32_t tmem_addr) {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem_addr) : "memory");
+}
+// the 1024-byte aligned start of the dynamic shared memory (generic and shared address)
+__device__ __forceinline__ uint8_t* tc05_smem(uint8_t* smraw, uint32_t& base) {
+    const uint32_t raw = static_cast<uint32_t>(__cvta_generic_to_shared(smraw));
+    base = (raw + 1023u) & ~1023u;
+    return smraw + (base - raw);
 }
 
 }  // namespace holo

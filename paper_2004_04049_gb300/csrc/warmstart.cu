@@ -601,16 +601,18 @@ extern "C" int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, cons
 namespace holo {
 int ospr_tc05_fault(int* out, bool clear);
 int ospr_persistent_fault(int* out, bool clear);
+int gs_tc05_fault(int* out, bool clear);
 }
 
 extern "C" int holo_tc_status(int* fault, int clear) {
     clear_error();
     if (!fault) return fail(HOLO_EINVAL, "holo_tc_status: NULL output");
-    int a = 0, b = 0, c = 0;
+    int a = 0, b = 0, c = 0, d = 0;
     int rc = conv3x3_tc05_fault(&a, clear != 0);
     if (rc) return rc;
     if ((rc = holo::ospr_tc05_fault(&b, clear != 0))) return rc;
     if ((rc = holo::ospr_persistent_fault(&c, clear != 0))) return rc;
-    *fault = a | b | c;
+    if ((rc = holo::gs_tc05_fault(&d, clear != 0))) return rc;
+    *fault = a | b | c | d;
     return HOLO_OK;
 }
