@@ -240,9 +240,9 @@ def measured_instructions(family, kernel, grid_y):
 def launch_signature(family, tuning, chunk, groups):
     """Template instance and grid.y of one float32 launch of an OSPR pass at H x W."""
     ci, cf, rv = tuning["col_ifft_variant"], tuning["col_fft_variant"], tuning["row_variant"]
-    return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {ci}, 0>", chunk),
-            "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cf}, 0>", groups),
-            "ospr_row": (f"k_ospr_row<{W}, {rv}, 1, 0, 0>", chunk)}.get(family, (None, None))
+    return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {ci}>", chunk),
+            "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cf}>", groups),
+            "ospr_row": (f"k_ospr_row<{W}, {rv}, 1, 0>", chunk)}.get(family, (None, None))
 
 
 # ------------------------------------------------------------------ our arm ----

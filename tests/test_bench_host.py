@@ -52,7 +52,7 @@ def _ncu_csv(path, rows):
 
 def test_traffic_record_round_trip(bench, tmp_path, monkeypatch):
     csv_path = tmp_path / "t.csv"
-    kernel = "void holo::k_ospr_col_ifft<1024, 0, 0>(holo::OsprArgs)"
+    kernel = "void holo::k_ospr_col_ifft<1024, 0>(holo::OsprArgs)"
     _ncu_csv(csv_path, [(kernel, "(64, 12, 1)", "dram__bytes_read.sum", "4,000,000"),
                         (kernel, "(64, 12, 1)", "dram__bytes_write.sum", "40,000,000"),
                         (kernel, "(64, 12, 1)", "smsp__inst_executed.sum", "37,000,000"),
@@ -61,29 +61,29 @@ def test_traffic_record_round_trip(bench, tmp_path, monkeypatch):
     out = tmp_path / "traffic.json"
     bench.record_traffic(str(csv_path), "ncu ...", str(out))
     rec = json.loads(out.read_text())["ospr_col_ifft"]
-    assert rec["kernel"] == "k_ospr_col_ifft<1024, 0, 0>"     # namespace dropped
+    assert rec["kernel"] == "k_ospr_col_ifft<1024, 0>"     # namespace dropped
     assert rec["dram__bytes_read.sum"] == 4e6 and rec["dram__bytes_write.sum"] == 4e7
     assert rec["sources"] == bench.sources_digest("ospr_col_ifft")
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(out))
-    traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0, 0>", 12)
+    traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 12)
     assert traffic == 4.4e7
-    assert bench.measured_instructions("ospr_col_ifft", "k_ospr_col_ifft<1024, 0, 0>", 12) == 3.7e7
+    assert bench.measured_instructions("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 12) == 3.7e7
     # another tile variant or pairs per launch than the capture's: no traffic
     traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 1, 0>", 12)
     assert traffic is None and "capture is of" in why
-    traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0, 0>", 8)
+    traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 8)
     assert traffic is None
     # a record whose kernel sources changed since the capture no longer applies
     data = json.loads(out.read_text())
     data["ospr_col_ifft"]["sources"] = "0" * 16
     out.write_text(json.dumps(data))
-    traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0, 0>", 12)
+    traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 12)
     assert traffic is None and "changed" in why
 
 
 def test_launch_signatures(bench):
     t = {"col_ifft_variant": 1, "col_fft_variant": 2, "row_variant": 0}
-    assert bench.launch_signature("ospr_col_ifft", t, 12, 2) == ("k_ospr_col_ifft<1024, 1, 0>", 12)
-    assert bench.launch_signature("ospr_col_fft", t, 12, 2) == ("k_ospr_col_fft<1024, 2, 0>", 2)
-    assert bench.launch_signature("ospr_row", t, 12, 2) == ("k_ospr_row<1024, 0, 1, 0, 0>", 12)
+    assert bench.launch_signature("ospr_col_ifft", t, 12, 2) == ("k_ospr_col_ifft<1024, 1>", 12)
+    assert bench.launch_signature("ospr_col_fft", t, 12, 2) == ("k_ospr_col_fft<1024, 2>", 2)
+    assert bench.launch_signature("ospr_row", t, 12, 2) == ("k_ospr_row<1024, 0, 1, 0>", 12)
     assert bench.launch_signature("replay_error", t, 12, 2) == (None, None)
