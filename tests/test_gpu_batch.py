@@ -67,6 +67,31 @@ def test_batch_equals_per_frame(cuda):
     _check(bufs, _per_frame(cuda, bufs))
 
 
+@pytest.mark.parametrize("prec", [holo.HOLO_FP16X2, holo.HOLO_BF16X2])
+def test_batch_tensor_core_equals_per_frame(cuda, prec):
+    """Frames of the tensor-core shapes in one batch call in a split precision equal the
+    per-frame calls in that precision (same tcgen05 kernels, internal streams)."""
+    specs = [(1024, 1024, 6, 10007, 21), (2048, 1024, 3, 4099, 22), (1024, 2048, 4, 0, 23)]
+    bufs, descs = [], []
+    for k, (H, W, N, L, seed) in enumerate(specs):
+        b = _alloc(cuda, (H, W, N, L, seed), k)
+        bufs.append(b)
+        descs.append(holo.frame_desc(b["T"], H, W, N, b["codes"], L, 256, seed, L > 0, 0, 0,
+                                     b["bits"], b["I"], b["err"]))
+    arr = holo.frame_array(descs)
+    holo.holo_tc_status(clear=True)
+    ws = torch.empty(holo.ospr_batch_workspace_size(arr, prec), dtype=torch.uint8, device=cuda)
+    holo.ospr_generate_batch(arr, prec, ws)
+    torch.cuda.synchronize()
+    for k, ((H, W, N, L, seed), b) in enumerate(zip(specs, bufs)):
+        codes = pipeline.lut(seed, L, device=cuda) if L > 0 else None
+        bits, I = pipeline.ospr(b["T"], N, codes, L, 256, seed, precision=prec)
+        err = pipeline.error(I, b["T"])
+        torch.cuda.synchronize()
+        assert torch.equal(b["bits"], bits) and torch.equal(b["I"], I) and torch.equal(b["err"], err), k
+    assert holo.holo_tc_status() == 0
+
+
 def test_graph_replays_batch(cuda):
     bufs = [_alloc(cuda, s, k) for k, s in enumerate(FRAMES)]
     arr = _descs(bufs)

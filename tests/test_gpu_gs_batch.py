@@ -18,14 +18,15 @@ from synthetic import blob_target, noise_target
 pytestmark = pytest.mark.gpu
 
 
-def _batch(cuda, T, iters, levels=256, codes=None, L=0, seed=0, start=0, init=None, states_in=None):
+def _batch(cuda, T, iters, levels=256, codes=None, L=0, seed=0, start=0, init=None, states_in=None,
+           precision=holo.HOLO_FP32):
     B, H, W = T.shape
-    ws = torch.empty(holo.gs_batch_workspace_size(B, H, W, iters), dtype=torch.uint8, device=cuda)
+    ws = torch.empty(holo.gs_batch_workspace_size(B, H, W, iters, precision), dtype=torch.uint8, device=cuda)
     out = {"codes": torch.empty((B, H, W), dtype=torch.uint8, device=cuda),
            "replay": torch.empty((B, H, W), dtype=torch.float32, device=cuda),
            "err": torch.empty((B, iters), dtype=torch.float64, device=cuda),
            "state": torch.empty((B, H, W, 2), dtype=torch.float32, device=cuda)}
-    holo.gs_iterate_batch(T, B, H, W, iters, levels, init, codes, L, 256, seed, start, holo.HOLO_FP32,
+    holo.gs_iterate_batch(T, B, H, W, iters, levels, init, codes, L, 256, seed, start, precision,
                           out["codes"], out["replay"], out["err"], states_in, out["state"], ws)
     torch.cuda.synchronize()
     return out
@@ -46,6 +47,26 @@ def test_batch_equals_per_target_calls(cuda, H, W, B, iters, levels):
         assert torch.equal(got["replay"][b], ref["replay"]), b
         assert torch.equal(got["err"][b], ref["err"]), b
         assert torch.equal(got["state"][b], ref["state"]), b
+
+
+@pytest.mark.parametrize("prec", [holo.HOLO_FP16X2, holo.HOLO_BF16X2])
+def test_batch_tensor_core_equals_per_target_calls(cuda, prec):
+    """The tensor-core passes take the target from grid.y like the float32 ones: a batch of
+    a 1024x2048 and a flipped copy equals two gs_iterate calls in the same precision."""
+    H, W, iters = 1024, 2048, 2
+    t0 = torch.from_numpy(blob_target(H, W, 3300)).to(cuda)
+    T = torch.stack([t0, torch.flip(t0, dims=[1])]).contiguous()
+    L, seed = 10007, 6
+    codes = pipeline.lut(seed, L, device=cuda)
+    holo.holo_tc_status(clear=True)
+    got = _batch(cuda, T, iters, 256, codes, L, seed, 0, precision=prec)
+    for b in range(2):
+        ref = pipeline.gs(T[b], iters, 256, codes, L, 256, seed, start=b * H * W, want_state=True, precision=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(got["codes"][b], ref["codes"]), b
+        assert torch.equal(got["err"][b], ref["err"]), b
+        assert torch.equal(got["state"][b], ref["state"]), b
+    assert holo.holo_tc_status() == 0
 
 
 def test_batch_with_caller_phases_and_states(cuda):
