@@ -319,8 +319,10 @@ __device__ __forceinline__ void ospr_col_ifft_body(const OsprArgs& a, int tile, 
     for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
 }
 
+// (256-thread tiles are held to 128 registers, two CTAs per SM)
 template <int NC, int V>
-__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
+__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC,
+                                  (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC <= 256 ? 2 : 1)
 k_ospr_col_ifft(OsprArgs a) {
     ospr_col_ifft_body<NC, V>(a, int(blockIdx.x), int(blockIdx.y));
 }
@@ -428,8 +430,10 @@ __device__ __forceinline__ void ospr_col_fft_body(const OsprArgs& a, int tile, i
     }
 }
 
+// (256-thread tiles are held to 128 registers, two CTAs per SM)
 template <int NC, int V>
-__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC)
+__global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC,
+                                  (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC <= 256 ? 2 : 1)
 k_ospr_col_fft(OsprArgs a) {
     ospr_col_fft_body<NC, V>(a, int(blockIdx.x), int(blockIdx.y));
 }
