@@ -32,13 +32,54 @@
 namespace holo {
 
 // ---------------------------------------------------------------- finalize ----
-// I(k) = I(-k) = (sum_g S_g(k) + S_g(-k)) * scale: one thread per pixel pair {k, -k}
-// reads both accumulators once and writes both outputs. Thread q handles pixel q of the
-// first half of the raster (rows 0 .. H/2) whose mirror lies at or after it.
-__global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, int W,
+// I(k) = I(-k) = (sum_g S_g(k) + S_g(-k)) * scale for the pixel pairs {k, -k}, in the order
+// of ospr_finalize_pixel (the same bits). Thread q takes the four pixels 4q .. 4q+3 of the
+// first half of the raster (rows 0 .. H/2; W >= 64 keeps them in one row): one float4 load
+// per group of their own accumulators, scalar loads of the mirrors (the mirror run is
+// descending and one pixel off the float4 grid), a float4 store of their outputs (scalar
+// stores into a replay buffer that is not 16-byte aligned) and scalar stores of the
+// mirrors' (P < 2^31: 32-bit indices). In rows 0 and H/2 a pixel whose
+// mirror lies before it is left to the mirror.
+__global__ void k_ospr_finalize(const float* __restrict__ S, int groups, int H, int W, int log2W,
                                 float scale, float* __restrict__ I) {
     pdl_wait();
-    ospr_finalize_pixel(S, groups, H, W, scale, I, size_t(blockIdx.x) * blockDim.x + threadIdx.x);
+    const uint32_t P = uint32_t(H) * uint32_t(W);
+    const uint32_t p0 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (p0 >= P / 2 + uint32_t(W)) return;
+    const uint32_t r = p0 >> log2W, c0 = p0 & uint32_t(W - 1);
+    const uint32_t rm = (uint32_t(H) - r) & uint32_t(H - 1);
+    uint32_t pm[4];
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pm[k] = rm * uint32_t(W) + ((uint32_t(W) - c0 - uint32_t(k)) & uint32_t(W - 1));
+    for (int g = 0; g < groups; ++g) {
+        const float* Sg = S + size_t(g) * P;
+        const float4 own = __ldg(reinterpret_cast<const float4*>(Sg + p0));
+        s[0] += own.x + __ldg(Sg + pm[0]);
+        s[1] += own.y + __ldg(Sg + pm[1]);
+        s[2] += own.z + __ldg(Sg + pm[2]);
+        s[3] += own.w + __ldg(Sg + pm[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] *= scale;
+    const bool edge = r == 0 || r == uint32_t(H / 2);   // rows whose mirrors lie in the same row
+    if (!edge) {
+        if ((reinterpret_cast<uintptr_t>(I) & 15) == 0) {
+            *reinterpret_cast<float4*>(I + p0) = make_float4(s[0], s[1], s[2], s[3]);
+        } else {   // a caller buffer aligned to its float only
+#pragma unroll
+            for (int k = 0; k < 4; ++k) I[p0 + k] = s[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) I[pm[k]] = s[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (pm[k] >= p0 + uint32_t(k)) {
+                I[p0 + k] = s[k];
+                I[pm[k]] = s[k];
+            }
+    }
 }
 
 // Fresnel replay: no twin symmetry, I(k) = scale * sum_g S_g(k)
@@ -238,10 +279,12 @@ static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_repla
         const size_t P = size_t(a.H) * a.W;
         const float scale = float(1.0 / (2.0 * double(a.N) * double(P)));
         const int threads = 256;
-        const int blocks = int((P / 2 + a.W + threads - 1) / threads);
+        const size_t quads = (P / 2 + a.W) / 4;   // W >= 64: the half raster is whole quads
+        const int blocks = int((quads + threads - 1) / threads);
         Launch ln("ospr_finalize", st);
         const cudaError_t le = launch_pdl(k_ospr_finalize, dim3(blocks), dim3(threads), 0, st,
-                                          static_cast<const float*>(a.sacc), pl.groups, a.H, a.W, scale, d_replay);
+                                          static_cast<const float*>(a.sacc), pl.groups, a.H, a.W, log2i(a.W),
+                                          scale, d_replay);
         if ((rc = ln.done("ospr_finalize launch", le))) return rc;
     }
     return HOLO_OK;
