@@ -160,6 +160,39 @@ def test_batch_with_host_buffers(cuda):
     assert ei.value.status == holo.HOLO_EINVAL
 
 
+def test_batch_with_host_buffers_more_frames_than_streams(cuda):
+    """Twelve frames on the library's eight internal streams (four streams run two frames,
+    the second one's target copied in after the first one's results went out). Two calls
+    in a row, the second with other targets, each equal to the device-resident batch."""
+    specs = FRAMES + [(H, W, N, L, seed + 100) for (H, W, N, L, seed) in FRAMES]
+    bufs = [_alloc(cuda, sp, k) for k, sp in enumerate(specs)]
+    arr = holo.frame_array([holo.frame_desc(b["T"], H, W, N, b["codes"], L, 256, seed, L > 0, 0, 0,
+                                            b["bits"], b["I"], b["err"])
+                            for (H, W, N, L, seed), b in zip(specs, bufs)])
+    ws = torch.empty(holo.ospr_batch_workspace_size(arr), dtype=torch.uint8, device=cuda)
+    for rnd in range(2):
+        if rnd == 1:
+            for b in bufs:
+                b["T"].copy_(torch.flip(b["T"], dims=[1]))
+        holo.ospr_generate_batch(arr, holo.HOLO_FP32, ws)
+        torch.cuda.synchronize()
+        ref = [(b["bits"].cpu(), b["I"].cpu(), b["err"].cpu()) for b in bufs]
+        h, hosts = [], []
+        for b in bufs:
+            o = {"T": b["T"].cpu().pin_memory(), "bits": torch.zeros(b["bits"].shape, dtype=torch.int32).pin_memory(),
+                 "I": torch.zeros(b["I"].shape, dtype=torch.float32).pin_memory(),
+                 "err": torch.zeros(3, dtype=torch.float64).pin_memory()}
+            b["T"].zero_()
+            h.append(o)
+            hosts.append(holo.frame_host(o["T"], o["bits"], o["I"], o["err"]))
+        holo.ospr_generate_batch_host(arr, holo.frame_host_array(hosts), holo.HOLO_FP32, ws)
+        torch.cuda.synchronize()
+        for k, (o, r) in enumerate(zip(h, ref)):
+            assert torch.equal(o["bits"], r[0]) and torch.equal(o["I"], r[1]) and torch.equal(o["err"], r[2]), \
+                (rnd, k)
+            assert torch.equal(bufs[k]["T"].cpu(), o["T"]), (rnd, k)   # the target was copied in
+
+
 def test_batch_calls_from_two_threads(cuda):
     # two host threads issue batch calls at the same time, each on its own stream with its
     # own frames and workspace; the calls share the library's internal streams and events,

@@ -144,6 +144,24 @@ def test_bits_only_and_replay_only(cuda):
     assert torch.equal(I_full, I_only)
 
 
+@pytest.mark.parametrize("H,W", [(128, 256), (64, 64)])
+def test_replay_into_unaligned_buffer(cuda, H, W):
+    """The finalize stores four pixels at once into a 16-byte aligned replay buffer and
+    falls back to single stores otherwise: a replay buffer one float into a larger one
+    gets the same bits as an aligned one, and nothing outside it is touched."""
+    T = blob_target(H, W, 1009)
+    t = torch.from_numpy(T).to(cuda)
+    codes = pipeline.lut(3, 1031, device=cuda)
+    _, I_ref = pipeline.ospr(t, 7, codes, 1031)
+    big = torch.full((H * W + 2,), -7.0, dtype=torch.float32, device=cuda)
+    view = big[1:1 + H * W].view(H, W)
+    assert view.data_ptr() % 16 != 0
+    pipeline.ospr(t, 7, codes, 1031, out_replay=view)
+    torch.cuda.synchronize()
+    assert torch.equal(view, I_ref)
+    assert big[0].item() == -7.0 and big[-1].item() == -7.0
+
+
 def test_deterministic(cuda):
     H = W = 256
     T = blob_target(H, W, 1007)
