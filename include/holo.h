@@ -344,9 +344,13 @@ typedef struct holo_frame_host {
 
 /*
  * ospr_generate_batch_host - ospr_generate_batch with each frame's host-to-device and
- * device-to-host copies issued on that frame's internal stream around its work, so that
- * one frame's copies overlap other frames' kernels. Page-locked host buffers make the
- * copies asynchronous (pageable ones are copied synchronously by CUDA). The host buffers
+ * device-to-host copies: the target is copied in on the frame's internal stream before its
+ * work; its results go out on a copy-out stream of that internal stream, the hologram bits
+ * as soon as the last row pass has written them (while the frame's replay passes and
+ * error still run), the replay and the error once the frame is done. So the copies
+ * overlap kernels and hold up neither the end of their frame nor the next frame of the
+ * internal stream. Page-locked host buffers make the copies asynchronous (pageable ones
+ * are copied synchronously by CUDA). The host buffers
  * must stay valid, and untouched by the caller, until stream `s` passes the call. Frames
  * must not share a d_target (each frame's copy writes it). HOLO_EINVAL for a NULL table
  * or a host output whose device buffer is NULL; other errors as ospr_generate_batch.

@@ -16,6 +16,12 @@
 
 namespace holo {
 
+// ospr.cu: ospr_generate with an event recorded once the last hologram bits are written
+int ospr_generate_ev(const float* d_target, int H, int W, int N, const uint8_t* d_codes, int64_t L, int levels,
+                     uint64_t seed, int64_t start_index, int64_t subframe_stride, int precision,
+                     uint32_t* d_holo_bits, float* d_replay, void* d_ws, size_t ws_bytes, holo_stream_t s,
+                     cudaEvent_t bits_ready);
+
 constexpr int kMaxBatchStreams = 32;
 
 static int batch_stream_count() {
@@ -31,10 +37,15 @@ static int batch_stream_count() {
 // the enqueue section of batch calls on the device (fork record to join wait), so that
 // calls from several host threads, or an eager call during another thread's graph
 // capture, never interleave their work on the shared streams and events
+// ospr_generate_batch_host also uses one copy-out stream per internal stream and two
+// events per frame (grown on demand, under run_mu)
 struct DeviceStreams {
     cudaStream_t st[kMaxBatchStreams];
     cudaEvent_t fork;
     cudaEvent_t join[kMaxBatchStreams];
+    cudaStream_t copy_out[kMaxBatchStreams];
+    cudaEvent_t copy_out_join[kMaxBatchStreams];
+    std::vector<cudaEvent_t> frame_ev;
     bool ready = false;
     std::mutex run_mu;
 };
@@ -50,9 +61,11 @@ static int device_streams(DeviceStreams** out) {
     DeviceStreams& ds = g_streams[dev];
     if (!ds.ready) {
         for (int i = 0; i < kMaxBatchStreams; ++i) {
-            if ((e = cudaStreamCreateWithFlags(&ds.st[i], cudaStreamNonBlocking)) != cudaSuccess)
+            if ((e = cudaStreamCreateWithFlags(&ds.st[i], cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaStreamCreateWithFlags(&ds.copy_out[i], cudaStreamNonBlocking)) != cudaSuccess)
                 return cuda_status(e, "batch: cudaStreamCreate");
-            if ((e = cudaEventCreateWithFlags(&ds.join[i], cudaEventDisableTiming)) != cudaSuccess)
+            if ((e = cudaEventCreateWithFlags(&ds.join[i], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&ds.copy_out_join[i], cudaEventDisableTiming)) != cudaSuccess)
                 return cuda_status(e, "batch: cudaEventCreate");
         }
         if ((e = cudaEventCreateWithFlags(&ds.fork, cudaEventDisableTiming)) != cudaSuccess)
@@ -129,11 +142,28 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
     int rc = device_streams(&ds);
     if (rc) return rc;
     std::lock_guard<std::mutex> run_lock(ds->run_mu);
-    cudaError_t e = cudaEventRecord(ds->fork, s);
-    if (e != cudaSuccess) return cuda_status(e, "batch: fork record");
-    for (int k = 0; k < pl.streams; ++k)
+    cudaError_t e;
+    if (io) {   // two events per frame: its bits are written, its work is done
+        while (ds->frame_ev.size() < 2 * size_t(n)) {
+            cudaEvent_t ev;
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_status(e, "batch: cudaEventCreate");
+            ds->frame_ev.push_back(ev);
+        }
+    }
+    if ((e = cudaEventRecord(ds->fork, s)) != cudaSuccess) return cuda_status(e, "batch: fork record");
+    for (int k = 0; k < pl.streams; ++k) {
         if ((e = cudaStreamWaitEvent(ds->st[k], ds->fork, 0)) != cudaSuccess) return cuda_status(e, "batch: fork wait");
+        if (io && (e = cudaStreamWaitEvent(ds->copy_out[k], ds->fork, 0)) != cudaSuccess)
+            return cuda_status(e, "batch: fork wait");
+    }
+    // With host buffers each frame's results go out on the copy-out stream of its internal
+    // stream: the hologram bits as soon as the last row pass has written them (while the
+    // frame's replay passes and error still run), the replay and the error once the frame
+    // is done. The copies then neither wait for the end of the frame nor hold up the next
+    // frame of the internal stream (frames own their outputs).
     int first_rc = HOLO_OK;
+    int frame_no = 0;
     for (int i : pl.order) {
         const holo_frame_desc& d = f[i];
         const int k = pl.stream_of[i];
@@ -150,9 +180,13 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
                 first_rc = fail(rc, "batch frame %d: %s", i, holo_last_error());
                 break;
             }
-        if ((rc = ospr_generate(d.d_target, d.H, d.W, d.N, d.d_codes, d.L, d.levels, d.seed, d.start_index,
-                                d.subframe_stride, precision, d.d_holo_bits, d.d_replay, slot + pl.ospr_off,
-                                pl.err_off - pl.ospr_off, hs))) {
+        cudaEvent_t ev_bits = io ? ds->frame_ev[2 * frame_no] : nullptr;
+        cudaEvent_t ev_done = io ? ds->frame_ev[2 * frame_no + 1] : nullptr;
+        ++frame_no;
+        const bool bits_early = io && io[i].h_holo_bits && d.d_holo_bits;
+        if ((rc = ospr_generate_ev(d.d_target, d.H, d.W, d.N, d.d_codes, d.L, d.levels, d.seed, d.start_index,
+                                   d.subframe_stride, precision, d.d_holo_bits, d.d_replay, slot + pl.ospr_off,
+                                   pl.err_off - pl.ospr_off, hs, bits_early ? ev_bits : nullptr))) {
             first_rc = fail(rc, "batch frame %d: %s", i, holo_last_error());
             break;
         }
@@ -162,12 +196,27 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
             break;
         }
         if (io) {
+            cudaStream_t co = ds->copy_out[k];
             const size_t words = size_t(d.N) * (P / 32);
-            if ((rc = frame_copy(io[i].h_holo_bits, d.d_holo_bits, words * sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                                 ds->st[k], i, "batch: bits copy")) ||
-                (rc = frame_copy(io[i].h_replay, d.d_replay, P * sizeof(float), cudaMemcpyDeviceToHost, ds->st[k], i,
+            if (bits_early) {
+                if ((e = cudaStreamWaitEvent(co, ev_bits, 0)) != cudaSuccess) {
+                    first_rc = cuda_status(e, "batch: bits copy event");
+                    break;
+                }
+                if ((rc = frame_copy(io[i].h_holo_bits, d.d_holo_bits, words * sizeof(uint32_t),
+                                     cudaMemcpyDeviceToHost, co, i, "batch: bits copy"))) {
+                    first_rc = rc;
+                    break;
+                }
+            }
+            if ((e = cudaEventRecord(ev_done, ds->st[k])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(co, ev_done, 0)) != cudaSuccess) {
+                first_rc = cuda_status(e, "batch: result copy event");
+                break;
+            }
+            if ((rc = frame_copy(io[i].h_replay, d.d_replay, P * sizeof(float), cudaMemcpyDeviceToHost, co, i,
                                  "batch: replay copy")) ||
-                (rc = frame_copy(io[i].h_err, d.d_err, 3 * sizeof(double), cudaMemcpyDeviceToHost, ds->st[k], i,
+                (rc = frame_copy(io[i].h_err, d.d_err, 3 * sizeof(double), cudaMemcpyDeviceToHost, co, i,
                                  "batch: error copy"))) {
                 first_rc = rc;
                 break;
@@ -179,6 +228,12 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
     for (int k = 0; k < pl.streams; ++k) {
         if ((e = cudaEventRecord(ds->join[k], ds->st[k])) != cudaSuccess) return cuda_status(e, "batch: join record");
         if ((e = cudaStreamWaitEvent(s, ds->join[k], 0)) != cudaSuccess) return cuda_status(e, "batch: join wait");
+        if (io) {
+            if ((e = cudaEventRecord(ds->copy_out_join[k], ds->copy_out[k])) != cudaSuccess)
+                return cuda_status(e, "batch: join record");
+            if ((e = cudaStreamWaitEvent(s, ds->copy_out_join[k], 0)) != cudaSuccess)
+                return cuda_status(e, "batch: join wait");
+        }
     }
     return first_rc;
 }

@@ -248,21 +248,32 @@ static int check_shape(const char* who, int H, int W) {
     return HOLO_OK;
 }
 
-// chunks of sub-frame pairs through the three passes, then the symmetrising finalize
-static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_replay, cudaStream_t st) {
+// chunks of sub-frame pairs through the three passes, then the symmetrising finalize;
+// `bits_ready` (optional) is recorded on the stream once the last row pass, which writes
+// the last hologram bits, is queued
+static int ospr_run(OsprArgs& a, const OsprPlan& pl, bool replay, float* d_replay, cudaStream_t st,
+                    cudaEvent_t bits_ready = nullptr) {
     int rc;
     for (int first = 0; first < pl.npairs; first += pl.chunk) {
         a.first_pair = first;
         a.pairs = pl.npairs - first < pl.chunk ? pl.npairs - first : pl.chunk;
         a.accumulate = first > 0;
+        const bool last = first + a.pairs >= pl.npairs;
         if (pl.prec == HOLO_FP32) {
             if ((rc = ospr_run_col_ifft(a, pl.ci_v, st))) return rc;
             if ((rc = ospr_run_row(a, pl.row_v, replay, st))) return rc;
-            if (replay && (rc = ospr_run_col_fft(a, pl.cf_v, st))) return rc;
         } else {
             if ((rc = ospr_run_col_ifft_tc(a, pl.prec, st))) return rc;
             if ((rc = ospr_run_row_tc(a, pl.prec, replay, st))) return rc;
-            if (replay && (rc = ospr_run_col_fft_tc(a, pl.prec, st))) return rc;
+        }
+        if (last && bits_ready) {
+            const cudaError_t e = cudaEventRecord(bits_ready, st);
+            if (e != cudaSuccess) return cuda_status(e, "ospr: bits event");
+        }
+        if (replay) {
+            if (pl.prec == HOLO_FP32) rc = ospr_run_col_fft(a, pl.cf_v, st);
+            else rc = ospr_run_col_fft_tc(a, pl.prec, st);
+            if (rc) return rc;
         }
     }
     if (replay && a.fresnel) {
@@ -318,12 +329,14 @@ static void ospr_design_rules(int64_t L, int N, int H, int W) {
 
 }  // namespace holo
 
-extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
-                             const uint8_t* d_codes, int64_t L, int levels, uint64_t seed,
-                             int64_t start_index, int64_t subframe_stride, int precision,
-                             uint32_t* d_holo_bits, float* d_replay,
-                             void* d_ws, size_t ws_bytes, holo_stream_t s) {
-    clear_error();
+namespace holo {
+
+// ospr_generate, with an optional event recorded on s once the last hologram bits are
+// written (the batch with host buffers starts their copy there)
+int ospr_generate_ev(const float* d_target, int H, int W, int N, const uint8_t* d_codes, int64_t L, int levels,
+                     uint64_t seed, int64_t start_index, int64_t subframe_stride, int precision,
+                     uint32_t* d_holo_bits, float* d_replay, void* d_ws, size_t ws_bytes, holo_stream_t s,
+                     cudaEvent_t bits_ready) {
     const char* who = "ospr_generate";
     int rc = check_shape(who, H, W);
     if (rc) return rc;
@@ -362,9 +375,22 @@ extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
     a.tc05b = tab.tc05b[precision];
     a.fresnel = 0;
     a.chirp_y = a.chirp_x = nullptr;
-    if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s)))) return rc;
+    if ((rc = ospr_run(a, pl, d_replay != nullptr, d_replay, reinterpret_cast<cudaStream_t>(s), bits_ready)))
+        return rc;
     ospr_design_rules(L, N, H, W);
     return HOLO_OK;
+}
+
+}  // namespace holo
+
+extern "C" int ospr_generate(const float* d_target, int H, int W, int N,
+                             const uint8_t* d_codes, int64_t L, int levels, uint64_t seed,
+                             int64_t start_index, int64_t subframe_stride, int precision,
+                             uint32_t* d_holo_bits, float* d_replay,
+                             void* d_ws, size_t ws_bytes, holo_stream_t s) {
+    clear_error();
+    return ospr_generate_ev(d_target, H, W, N, d_codes, L, levels, seed, start_index, subframe_stride, precision,
+                            d_holo_bits, d_replay, d_ws, ws_bytes, s, nullptr);
 }
 
 // Fresnel propagation: one sub-frame per field slot, so the plan of 2N sub-frames gives N
