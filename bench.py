@@ -481,9 +481,9 @@ def run_ours(args):
     # end to end through the public API: every frame's target copied in from page-locked
     # host memory and every frame's result copied back (the hologram bits and the error;
     # in a second measurement the replay image too), all inside one
-    # ospr_generate_batch_host call, which copies each target in on its frame's internal
-    # stream and the results out on copy-out streams (the bits as soon as the last row
-    # pass has written them), overlapping the kernels.
+    # ospr_generate_batch_host call, which copies the targets in on a copy-in stream in
+    # launch order and the results out on copy-out streams (the bits as soon as the last
+    # row pass has written them), overlapping the kernels.
     h_targets = [t.cpu().pin_memory() for t in targets]
     h_out = [{"bits": torch.empty((N_SF, P // 32), dtype=torch.int32).pin_memory(),
               "I": torch.empty((H, W), dtype=torch.float32).pin_memory(),

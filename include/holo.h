@@ -344,8 +344,9 @@ typedef struct holo_frame_host {
 
 /*
  * ospr_generate_batch_host - ospr_generate_batch with each frame's host-to-device and
- * device-to-host copies: the target is copied in on the frame's internal stream before its
- * work; its results go out on a copy-out stream of that internal stream, the hologram bits
+ * device-to-host copies: the targets are copied in on one internal copy-in stream in the
+ * frames' launch order, each frame's work waiting for its own target; its results go out
+ * on a copy-out stream of the frame's internal stream, the hologram bits
  * as soon as the last row pass has written them (while the frame's replay passes and
  * error still run), the replay and the error once the frame is done. So the copies
  * overlap kernels and hold up neither the end of their frame nor the next frame of the

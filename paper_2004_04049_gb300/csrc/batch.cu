@@ -37,12 +37,14 @@ static int batch_stream_count() {
 // the enqueue section of batch calls on the device (fork record to join wait), so that
 // calls from several host threads, or an eager call during another thread's graph
 // capture, never interleave their work on the shared streams and events
-// ospr_generate_batch_host also uses one copy-out stream per internal stream and two
-// events per frame (grown on demand, under run_mu)
+// ospr_generate_batch_host also uses one copy-in stream, one copy-out stream per internal
+// stream and three events per frame (grown on demand, under run_mu)
 struct DeviceStreams {
     cudaStream_t st[kMaxBatchStreams];
     cudaEvent_t fork;
     cudaEvent_t join[kMaxBatchStreams];
+    cudaStream_t copy_in;
+    cudaEvent_t copy_in_join;
     cudaStream_t copy_out[kMaxBatchStreams];
     cudaEvent_t copy_out_join[kMaxBatchStreams];
     std::vector<cudaEvent_t> frame_ev;
@@ -68,7 +70,10 @@ static int device_streams(DeviceStreams** out) {
                 (e = cudaEventCreateWithFlags(&ds.copy_out_join[i], cudaEventDisableTiming)) != cudaSuccess)
                 return cuda_status(e, "batch: cudaEventCreate");
         }
-        if ((e = cudaEventCreateWithFlags(&ds.fork, cudaEventDisableTiming)) != cudaSuccess)
+        if ((e = cudaStreamCreateWithFlags(&ds.copy_in, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_status(e, "batch: cudaStreamCreate");
+        if ((e = cudaEventCreateWithFlags(&ds.fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ds.copy_in_join, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_status(e, "batch: cudaEventCreate");
         ds.ready = true;
     }
@@ -143,8 +148,8 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
     if (rc) return rc;
     std::lock_guard<std::mutex> run_lock(ds->run_mu);
     cudaError_t e;
-    if (io) {   // two events per frame: its bits are written, its work is done
-        while (ds->frame_ev.size() < 2 * size_t(n)) {
+    if (io) {   // three events per frame: its target is in, its bits are written, its work is done
+        while (ds->frame_ev.size() < 3 * size_t(n)) {
             cudaEvent_t ev;
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
                 return cuda_status(e, "batch: cudaEventCreate");
@@ -157,11 +162,16 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
         if (io && (e = cudaStreamWaitEvent(ds->copy_out[k], ds->fork, 0)) != cudaSuccess)
             return cuda_status(e, "batch: fork wait");
     }
-    // With host buffers each frame's results go out on the copy-out stream of its internal
-    // stream: the hologram bits as soon as the last row pass has written them (while the
-    // frame's replay passes and error still run), the replay and the error once the frame
-    // is done. The copies then neither wait for the end of the frame nor hold up the next
-    // frame of the internal stream (frames own their outputs).
+    if (io && (e = cudaStreamWaitEvent(ds->copy_in, ds->fork, 0)) != cudaSuccess)
+        return cuda_status(e, "batch: fork wait");
+    // With host buffers the targets go in on the copy-in stream in launch order, ahead of
+    // the frames' work (each frame waits for its own target; frames own their targets), so
+    // the first frames start one target copy apart; each frame's results go out on the
+    // copy-out stream of its internal stream: the hologram bits as soon as the last row
+    // pass has written them (while the frame's replay passes and error still run), the
+    // replay and the error once the frame is done. The copies then neither wait for the
+    // end of the frame nor hold up the next frame of the internal stream (frames own
+    // their outputs).
     int first_rc = HOLO_OK;
     int frame_no = 0;
     for (int i : pl.order) {
@@ -170,19 +180,27 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
         char* slot = static_cast<char*>(d_ws) + size_t(k) * pl.slot_bytes;
         holo_stream_t hs = reinterpret_cast<holo_stream_t>(ds->st[k]);
         const size_t P = size_t(d.H) * size_t(d.W);
-        if (io && (rc = frame_copy(const_cast<float*>(d.d_target), io[i].h_target, P * sizeof(float),
-                                   cudaMemcpyHostToDevice, ds->st[k], i, "batch: target copy"))) {
-            first_rc = rc;
-            break;
+        cudaEvent_t ev_in = io ? ds->frame_ev[3 * frame_no] : nullptr;
+        cudaEvent_t ev_bits = io ? ds->frame_ev[3 * frame_no + 1] : nullptr;
+        cudaEvent_t ev_done = io ? ds->frame_ev[3 * frame_no + 2] : nullptr;
+        ++frame_no;
+        if (io && io[i].h_target) {
+            if ((rc = frame_copy(const_cast<float*>(d.d_target), io[i].h_target, P * sizeof(float),
+                                 cudaMemcpyHostToDevice, ds->copy_in, i, "batch: target copy"))) {
+                first_rc = rc;
+                break;
+            }
+            if ((e = cudaEventRecord(ev_in, ds->copy_in)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(ds->st[k], ev_in, 0)) != cudaSuccess) {
+                first_rc = cuda_status(e, "batch: target copy event");
+                break;
+            }
         }
         if (d.build_lut && d.L > 0)
             if ((rc = lut_build(d.seed, d.L, d.levels, d.d_codes, nullptr, hs))) {
                 first_rc = fail(rc, "batch frame %d: %s", i, holo_last_error());
                 break;
             }
-        cudaEvent_t ev_bits = io ? ds->frame_ev[2 * frame_no] : nullptr;
-        cudaEvent_t ev_done = io ? ds->frame_ev[2 * frame_no + 1] : nullptr;
-        ++frame_no;
         const bool bits_early = io && io[i].h_holo_bits && d.d_holo_bits;
         if ((rc = ospr_generate_ev(d.d_target, d.H, d.W, d.N, d.d_codes, d.L, d.levels, d.seed, d.start_index,
                                    d.subframe_stride, precision, d.d_holo_bits, d.d_replay, slot + pl.ospr_off,
@@ -234,6 +252,11 @@ static int run_batch(const holo_frame_desc* f, int n, int precision, void* d_ws,
             if ((e = cudaStreamWaitEvent(s, ds->copy_out_join[k], 0)) != cudaSuccess)
                 return cuda_status(e, "batch: join wait");
         }
+    }
+    if (io) {
+        if ((e = cudaEventRecord(ds->copy_in_join, ds->copy_in)) != cudaSuccess)
+            return cuda_status(e, "batch: join record");
+        if ((e = cudaStreamWaitEvent(s, ds->copy_in_join, 0)) != cudaSuccess) return cuda_status(e, "batch: join wait");
     }
     return first_rc;
 }
