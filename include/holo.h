@@ -191,9 +191,11 @@ int ospr_generate(const float* d_target, int H, int W, int N,
  * the current setting, so query it after changing it.
  * ospr_autotune times ospr_generate on synthetic data of this shape (a 10007-entry table)
  * for candidate settings (two sweeps of coordinate descent over the column IDFT variant,
- * row variant, column DFT variant, chunk and groups; each candidate the median of `reps`
- * runs after one warm-up, CUDA events on stream s; timings within 1% are a tie, won by the
- * setting with the smaller workspace), installs the fastest for this process
+ * row variant, column DFT variant, chunk and groups, starting from column DFT variant 1
+ * where the length has it, whose two CTAs per SM let batch frames share the SMs; each
+ * candidate the median of `reps` runs after one warm-up, CUDA events on stream s; timings
+ * within 1% are a tie, kept by the current setting unless the candidate's workspace is
+ * smaller), installs the fastest for this process
  * and, when the environment variable HOLO_TUNE_CACHE names a file, writes every installed
  * setting there (one JSON object per line), from where later processes read it. It
  * allocates and frees its own scratch (HOLO_ENOMEM if that fails) and synchronises s.

@@ -551,7 +551,11 @@ extern "C" int ospr_autotune(int H, int W, int N, int reps, holo_stream_t s, dou
         *ms = v[reps / 2];
         return HOLO_OK;
     };
-    OsprTuning best{0, 0, 0, kMaxChunkPairs < npairs ? kMaxChunkPairs : npairs, kMaxGroups};
+    // the descent starts from the 256-thread column DFT tiles (variant 1, two CTAs per SM):
+    // alone a frame times them within about 1% of variant 0, but in a batch they let
+    // other frames' CTAs share the SMs (14-frame 1024^2 step: 164.9 k against 160.9 k
+    // sub-frames/s), so a tie keeps them
+    OsprTuning best{0, col_variants(H) > 1 ? 1 : 0, 0, kMaxChunkPairs < npairs ? kMaxChunkPairs : npairs, kMaxGroups};
     float best_t = 0.f;
     if (!rc) rc = measure(best, &best_t);
     // coordinate descent, two sweeps: column IDFT tiles, row tiles, column DFT tiles,
