@@ -24,7 +24,9 @@ __host__ __device__ __forceinline__ uint32_t lfsr_step(uint32_t s) {
 // a * b mod p: shift-and-add over the 31 coefficients of b
 __host__ __device__ __forceinline__ uint32_t lfsr_mulmod(uint32_t a, uint32_t b) {
     uint32_t r = 0;
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
     for (int i = 0; i < 31; ++i) {
         r ^= (b & 1u) ? a : 0u;
         b >>= 1;
