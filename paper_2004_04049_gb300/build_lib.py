@@ -75,8 +75,11 @@ def build(verbose=False, extra_flags=(), jobs=None):
                 raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{out}")
     newest = max(os.path.getmtime(o) for o in objs)
     if todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+        # --no-undefined: a symbol one translation unit declares and no other defines
+        # fails the build here rather than the dlopen
         cmd = [nvcc, "-shared", "-o", LIB] + objs + ARCH + ["-cudart", "shared",
-                                                            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+                                                            "-Xlinker", "-rpath,/usr/local/cuda/lib64",
+                                                            "-Xlinker", "--no-undefined"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

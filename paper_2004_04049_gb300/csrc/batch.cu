@@ -16,12 +16,6 @@
 
 namespace holo {
 
-// ospr.cu: ospr_generate with an event recorded once the last hologram bits are written
-int ospr_generate_ev(const float* d_target, int H, int W, int N, const uint8_t* d_codes, int64_t L, int levels,
-                     uint64_t seed, int64_t start_index, int64_t subframe_stride, int precision,
-                     uint32_t* d_holo_bits, float* d_replay, void* d_ws, size_t ws_bytes, holo_stream_t s,
-                     cudaEvent_t bits_ready);
-
 constexpr int kMaxBatchStreams = 32;
 
 static int batch_stream_count() {

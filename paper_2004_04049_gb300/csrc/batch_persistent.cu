@@ -522,11 +522,6 @@ int ospr_persistent_fault(int* out, bool clear) {
 
 using namespace holo;
 
-struct holo_graph;
-namespace holo {
-holo_graph* make_holo_graph(cudaGraph_t graph, cudaGraphExec_t exec, int device, int64_t kernels);
-}
-
 extern "C" int ospr_batch_persistent_workspace_size(const holo_frame_desc* h_frames, int n_frames, size_t* bytes) {
     clear_error();
     if (!bytes) return fail(HOLO_EINVAL, "ospr_batch_persistent_workspace_size: NULL output");

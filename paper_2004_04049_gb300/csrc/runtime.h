@@ -93,6 +93,21 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr int kMinDim = 64;
 constexpr int kMaxDim = 4096;
 
+// ---- entry points shared between translation units (library-internal) -----
+// the bounded-wait flags of the tcgen05 DFT passes (ospr_tc.cu, gs.cu) and of the
+// persistent batch kernel (batch_persistent.cu): read, and cleared when `clear`
+int ospr_tc05_fault(int* out, bool clear);
+int gs_tc05_fault(int* out, bool clear);
+int ospr_persistent_fault(int* out, bool clear);
+// ospr_generate with an optional event recorded on s once the last hologram bits are
+// written (ospr.cu; the host-buffer batch starts their copy there)
+int ospr_generate_ev(const float* d_target, int H, int W, int N, const uint8_t* d_codes, int64_t L, int levels,
+                     uint64_t seed, int64_t start_index, int64_t subframe_stride, int precision,
+                     uint32_t* d_holo_bits, float* d_replay, void* d_ws, size_t ws_bytes, holo_stream_t s,
+                     cudaEvent_t bits_ready);
+// a holo_graph for a graph built in another translation unit (batch.cu defines the type)
+holo_graph* make_holo_graph(cudaGraph_t graph, cudaGraphExec_t exec, int device, int64_t kernels);
+
 // Sets the dynamic shared-memory limit of kernel `fn` on the current device once.
 int ensure_smem(const void* fn, size_t bytes, uint64_t* device_mask);
 

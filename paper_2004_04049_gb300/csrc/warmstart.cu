@@ -598,12 +598,6 @@ extern "C" int nn_conv3x3(int mode, int B, int H, int W, int Cin, int Cout, cons
     return conv3x3(a, mode, reinterpret_cast<cudaStream_t>(s), legacy);
 }
 
-namespace holo {
-int ospr_tc05_fault(int* out, bool clear);
-int ospr_persistent_fault(int* out, bool clear);
-int gs_tc05_fault(int* out, bool clear);
-}
-
 extern "C" int holo_tc_status(int* fault, int clear) {
     clear_error();
     if (!fault) return fail(HOLO_EINVAL, "holo_tc_status: NULL output");
