@@ -43,7 +43,7 @@ __device__ __forceinline__ uint64_t tc05_desc(uint32_t addr) {
 // kind::f16 instruction descriptor: fp16 (0) or bf16 (1) operands, float32 D, M = 128, N = 64
 template <int PREC>
 __host__ __device__ constexpr uint32_t tc05_idesc() {
-    return (1u << 4) | (uint32_t(PREC == 2 ? 1 : 0) << 7) | (uint32_t(PREC == 2 ? 1 : 0) << 10) |
+    return (1u << 4) | (uint32_t(PREC == kTcBf16 ? 1 : 0) << 7) | (uint32_t(PREC == kTcBf16 ? 1 : 0) << 10) |
            (uint32_t(64 >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 }
 
@@ -59,7 +59,7 @@ struct Tc05Group {
 
 template <int PREC>
 __device__ __forceinline__ uint32_t pack16(float a, float b, uint32_t& lo) {
-    if constexpr (PREC == 2) {
+    if constexpr (PREC == kTcBf16) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
         const float2 f = __bfloat1622float2(h);
         const __nv_bfloat162 l = __floats2bfloat162_rn(a - f.x, b - f.y);
@@ -184,8 +184,8 @@ __device__ __forceinline__ void line_fft_tc05(float2 (&v)[32], float2* buf, int 
                                              Tc05Group& g) {
     static_assert(N == 1024 || N == 2048, "tcgen05 line FFT: 1024 or 2048 points");
     constexpr int T = N / 32;
-    const float scale = PREC == 1 ? 1.f / 256.f : 1.f;
-    const float unscale = PREC == 1 ? 256.f : 1.f;
+    const float scale = PREC == kTcFp16 ? 1.f / 256.f : 1.f;
+    const float unscale = PREC == kTcFp16 ? 256.f : 1.f;
     // stage 0 (sub-transform length 1): DFT of elements t + T m, output m to 32 t + m
     dft32_tc05<PREC>(v, g, scale, unscale);
 #pragma unroll
