@@ -474,8 +474,9 @@ int gs_iterate_fresnel(const float* d_target, int H, int W, int iters, int level
  * With the LUT start, target b draws its initial phases at start_index + b*H*W + p: the
  * targets continue the table like consecutive frames (Fig. 3; Section 8's rule for GS
  * video: every frame gets fresh phases). Each target's results equal those of gs_iterate
- * with start_index + b*H*W. 1 <= B <= 65535 and B*H*W <= 2^31; other arguments and
- * errors as gs_iterate. gs_batch_workspace_size gives the workspace of B targets.
+ * with start_index + b*H*W, in either precision. 1 <= B <= 65535 and B*H*W <= 2^31; other
+ * arguments (the tensor-core precisions included) and errors as gs_iterate.
+ * gs_batch_workspace_size gives the workspace of B targets.
  */
 int gs_batch_workspace_size(int B, int H, int W, int iters, int precision, size_t* bytes);
 int gs_iterate_batch(const float* d_targets, int B, int H, int W, int iters, int levels,
