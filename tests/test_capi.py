@@ -94,6 +94,23 @@ def test_batch_workspace_is_host_only(lib):
     assert "frame 0" in str(ei.value)
 
 
+def test_persistent_workspace_is_host_only(lib):
+    # planning the persistent launch needs no GPU: slots sized for the largest frame, one
+    # slot per frame up to eight, plus counters, frame table and queue
+    def desc(H, W, N, replay=1 << 23):
+        return holo.frame_desc(1 << 20, H, W, N, 1 << 21, 1031, 256, 1, True, 0, 0, 1 << 22, replay, None)
+    one = holo.ospr_batch_persistent_workspace_size(holo.frame_array([desc(1024, 1024, 24)]))
+    three = holo.ospr_batch_persistent_workspace_size(holo.frame_array([desc(1024, 1024, 24)] * 3))
+    assert one >= holo.ospr_workspace_size(1024, 1024, 24) and three > 2 * one
+    mixed = holo.ospr_batch_persistent_workspace_size(holo.frame_array([desc(512, 512, 8), desc(2048, 2048, 4)]))
+    assert mixed >= 2 * holo.ospr_workspace_size(2048, 2048, 4)
+    for bad, status in [(desc(256, 256, 8), holo.HOLO_EUNSUPPORTED), (desc(1024, 1024, 8, None), holo.HOLO_EINVAL),
+                        (desc(1024, 1024, 0), holo.HOLO_EINVAL)]:
+        with pytest.raises(holo.HoloError) as ei:
+            holo.ospr_batch_persistent_workspace_size(holo.frame_array([desc(512, 512, 8), bad]))
+        assert ei.value.status == status and "frame 1" in str(ei.value)
+
+
 def test_tuning_set_get_host_only(lib):
     # 256-point columns have one tile variant: column variants fall back to 0; 512-point
     # rows keep variant 1
