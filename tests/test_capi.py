@@ -78,6 +78,14 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert rc == holo.HOLO_EINVAL
     rc = lib.replay_error(None, None, None, 4, 4, None, None, 0, None)
     assert rc == holo.HOLO_EINVAL
+    # the fixed-scratch variant checks its shape against the scratch before looking it up
+    for args, status in [((2048, 2048, 4, 0), holo.HOLO_EWORKSPACE), ((1024, 1024, 0, 0), holo.HOLO_EINVAL),
+                         ((1024, 1024, 4, holo.HOLO_BF16X2), holo.HOLO_EUNSUPPORTED),
+                         ((96, 512, 4, 0), holo.HOLO_EUNSUPPORTED)]:
+        H, W, N, prec = args
+        with pytest.raises(holo.HoloError) as ei:
+            holo.ospr_generate_noalloc(1 << 20, H, W, N, None, 0, 256, 0, 0, 0, prec, 1 << 22, None)
+        assert ei.value.status == status, args
     n = ctypes.c_uint64(0)
     assert lib.holo_launch_count(ctypes.byref(n)) == 0
 
