@@ -179,10 +179,14 @@ def test_training_reduces_loss(cuda, tmp_path):
         lab = torch.from_numpy(label).to(cuda)
         loss = torch.zeros(1, dtype=torch.float32, device=cuda)
         losses = []
-        for step in range(60):
+        for step in range(120):
             holo.ws_train_step(net, t, lab, 4, 1e-3, loss)
             losses.append(float(loss.item()))
-        assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+        # the weight gradients are summed with float atomics, so the trajectory differs from
+        # run to run, and under Adam the per-step loss oscillates on its way down (steps 20 to
+        # 60 range from ~0.5 of the start down to ~0.02); from step 80 on every run seen sits
+        # below 0.03 of the start: judge the median of the last ten of 120 steps, not one step
+        assert np.median(losses[-10:]) < 0.5 * losses[0], (losses[0], losses[-10:])
         path = tmp_path / "ws.bin"
         holo.ws_save(net, path)
         net2 = holo.ws_net_create(99, 1)
