@@ -196,6 +196,13 @@ def record_traffic(csv_path, command, out_path=TRAFFIC_FILE):
         if rec["kernel"] != name or rec["grid"] != r[gi]:
             continue   # first launch of the family only
         rec[r[mi]] = float(r[vi].replace(",", ""))
+    # work per launch: the grid's y (pairs, or groups for the column DFT); a one-dimensional
+    # grid (the column IDFT's one CTA per resident slot) runs the chunk the row pass of the
+    # same capture runs
+    for fam, rec in out.items():
+        rec["per_launch"] = _grid_y(rec["grid"])
+    if "ospr_col_ifft" in out and "ospr_row" in out and _grid_y(out["ospr_col_ifft"]["grid"]) == 1:
+        out["ospr_col_ifft"]["per_launch"] = out["ospr_row"]["per_launch"]
     old = {}
     if os.path.exists(out_path):
         with open(out_path) as fh:
@@ -207,8 +214,18 @@ def record_traffic(csv_path, command, out_path=TRAFFIC_FILE):
     print(json.dumps(out, indent=1))
 
 
-def measured_traffic(family, kernel, grid_y):
-    """DRAM bytes of one launch, or (None, why not)."""
+def _grid_y(grid):
+    gy = grid.strip("()").split(",")
+    return int(gy[1]) if len(gy) >= 2 else None
+
+
+def _record_per_launch(rec):
+    return rec.get("per_launch", _grid_y(rec.get("grid", "")))
+
+
+def measured_traffic(family, kernel, per_launch):
+    """DRAM bytes of one launch of `per_launch` pairs (groups for the column DFT), or
+    (None, why not)."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)[family]
@@ -216,29 +233,28 @@ def measured_traffic(family, kernel, grid_y):
         return None, "no ncu capture recorded"
     if rec.get("sources") != sources_digest(family):
         return None, "kernel sources changed since the capture"
-    gy = rec.get("grid", "").strip("()").split(",")
-    if rec.get("kernel") != kernel or len(gy) < 2 or int(gy[1]) != grid_y:
+    if rec.get("kernel") != kernel or _record_per_launch(rec) != per_launch:
         return None, f"capture is of {rec.get('kernel')} grid {rec.get('grid')}"
     return rec["dram__bytes_read.sum"] + rec["dram__bytes_write.sum"], \
         f"ncu capture of {kernel} grid {rec['grid']}: {rec['command']}"
 
 
-def measured_instructions(family, kernel, grid_y):
+def measured_instructions(family, kernel, per_launch):
     """Warp instructions of one launch from the ncu record (smsp__inst_executed.sum), or None."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)[family]
     except (OSError, ValueError, KeyError):
         return None
-    gy = rec.get("grid", "").strip("()").split(",")
-    if rec.get("sources") != sources_digest(family) or rec.get("kernel") != kernel or len(gy) < 2 \
-            or int(gy[1]) != grid_y:
+    if rec.get("sources") != sources_digest(family) or rec.get("kernel") != kernel \
+            or _record_per_launch(rec) != per_launch:
         return None
     return rec.get("smsp__inst_executed.sum")
 
 
 def launch_signature(family, tuning, chunk, groups):
-    """Template instance and grid.y of one float32 launch of an OSPR pass at H x W."""
+    """Template instance and work per launch (pairs; groups for the column DFT) of one
+    float32 launch of an OSPR pass at H x W."""
     ci, cf, rv = tuning["col_ifft_variant"], tuning["col_fft_variant"], tuning["row_variant"]
     return {"ospr_col_ifft": (f"k_ospr_col_ifft<{H}, {ci}>", chunk),
             "ospr_col_fft": (f"k_ospr_col_fft<{H}, {cf}>", groups),

@@ -4,15 +4,25 @@
 
 namespace holo {
 
+// looping kernels: one CTA per resident slot (at most one per tile), each over every G-th
+// tile; the others: one CTA per tile
 template <int NC, int V>
 static int launch_col_ifft(const OsprArgs& a, cudaStream_t st) {
     static uint64_t mask = 0;
+    static int resident[64] = {};
     constexpr size_t smem = col_ifft_smem_bytes<NC, V>();
+    constexpr int threads = (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC;
     int rc = ensure_smem((const void*)k_ospr_col_ifft<NC, V>, smem, &mask);
     if (rc) return rc;
-    dim3 grid(a.W / ColCfg<NC, V>::LPC, a.pairs);
+    const int tiles = a.W / ColCfg<NC, V>::LPC;
+    dim3 grid(tiles, a.pairs);
+    if constexpr (col_ifft_loops<NC, V>()) {
+        int slots = 0;
+        if ((rc = resident_ctas((const void*)k_ospr_col_ifft<NC, V>, threads, smem, resident, &slots))) return rc;
+        grid = dim3(tiles * a.pairs < slots ? tiles * a.pairs : slots);
+    }
     Launch ln("ospr_col_ifft", st);
-    const cudaError_t le = launch_pdl(k_ospr_col_ifft<NC, V>, grid, dim3((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC), smem, st, a);
+    const cudaError_t le = launch_pdl(k_ospr_col_ifft<NC, V>, grid, dim3(threads), smem, st, a);
     return ln.done("ospr_col_ifft launch", le);
 }
 

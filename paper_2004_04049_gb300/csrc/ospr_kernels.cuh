@@ -275,18 +275,14 @@ __device__ __forceinline__ void ospr_build_column(float2 (&v)[ColCfg<NC, V>::R],
 }
 
 // Pass 1 on column tile `tile` (LPC/2 mirror column pairs) of field slot `slot`; every
-// thread of the CTA (ColCfg threads) calls it.
+// thread of the CTA (ColCfg threads) calls it with the cos/sin table `cs` loaded and the
+// line buffers `lines` free (no thread still reading them). `trigger` lets the next kernel
+// launch once the tile's transforms are done.
 template <int NC, int V>
-__device__ __forceinline__ void ospr_col_ifft_body(const OsprArgs& a, int tile, int slot) {
+__device__ __forceinline__ void ospr_col_ifft_tile(const OsprArgs& a, int tile, int slot, const float2* cs,
+                                                   float2* lines, bool trigger) {
     constexpr int R = ColCfg<NC, V>::R, LPC = ColCfg<NC, V>::LPC, T = NC / R, S = col_stride<NC, V>();
     static_assert(stage_count(NC, R) > 1, "the line FFT's opening barrier guards the exchange buffer");
-    extern __shared__ float2 sm[];
-    float2* cs = sm;
-    float2* lines = sm + kCsSmemEntries;
-    load_cs_table(cs, a.cs256);
-    pdl_wait();   // the table and target may be written by the previous kernel
-    __syncthreads();
-
     const int lc = threadIdx.x % LPC, t = threadIdx.x / LPC;
     const int W = a.W;
     int c, pl;
@@ -313,18 +309,50 @@ __device__ __forceinline__ void ospr_col_ifft_body(const OsprArgs& a, int tile, 
             if (t > 0 || e > R / 2) v[e] = own[pad_index<R>(t + T * e)];
     }
     col_line_fft<NC, V, +1>(v, lines, lc, t, a);
-    pdl_trigger();
+    if (trigger) pdl_trigger();
     float2* z = a.zbuf + size_t(slot) * size_t(NC) * size_t(W);
 #pragma unroll
     for (int e = 0; e < R; ++e) z[size_t(t + T * e) * W + c] = v[e];
 }
 
+// One tile with the table loaded first (the persistent batch kernel's form).
+template <int NC, int V>
+__device__ __forceinline__ void ospr_col_ifft_body(const OsprArgs& a, int tile, int slot) {
+    extern __shared__ float2 sm[];
+    load_cs_table(sm, a.cs256);
+    pdl_wait();   // the table and target may be written by the previous kernel
+    __syncthreads();
+    ospr_col_ifft_tile<NC, V>(a, tile, slot, sm, sm + kCsSmemEntries, true);
+}
+
+// Pass 1 over the chunk's n = (W/LPC) x pairs tiles, item i being tile i mod (W/LPC) of
+// slot i / (W/LPC). Where col_ifft_loops holds the grid has one CTA per resident slot and
+// CTA b takes items b, b + G, b + 2G, ...: it loads the cos/sin table once, and the CTAs
+// running at one time write neighbouring tiles of one field, as a grid of one CTA per
+// tile would (1024-point columns of variant 0: 80.4 against 82.8 us per 12-pair launch at
+// 1024^2; longer columns and the other variants ran slower so, and keep one CTA per tile,
+// grid (W/LPC, pairs)).
 // (256-thread tiles are held to 128 registers, two CTAs per SM)
+template <int NC, int V>
+constexpr bool col_ifft_loops() { return V == 0 && NC <= 1024; }
+
 template <int NC, int V>
 __global__ void __launch_bounds__((NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC,
                                   (NC / ColCfg<NC, V>::R) * ColCfg<NC, V>::LPC <= 256 ? 2 : 1)
 k_ospr_col_ifft(OsprArgs a) {
-    ospr_col_ifft_body<NC, V>(a, int(blockIdx.x), int(blockIdx.y));
+    if constexpr (col_ifft_loops<NC, V>()) {
+        extern __shared__ float2 sm[];
+        load_cs_table(sm, a.cs256);
+        pdl_wait();   // the table and target may be written by the previous kernel
+        const int tiles = a.W / ColCfg<NC, V>::LPC;
+        const int n = tiles * a.pairs;
+        for (int i = blockIdx.x; i < n; i += gridDim.x) {
+            __syncthreads();   // the table is in place; the previous tile is done with the line buffers
+            ospr_col_ifft_tile<NC, V>(a, i % tiles, i / tiles, sm, sm + kCsSmemEntries, i + int(gridDim.x) >= n);
+        }
+    } else {
+        ospr_col_ifft_body<NC, V>(a, int(blockIdx.x), int(blockIdx.y));
+    }
 }
 
 // ------------------------------------------------------------------ pass 2 ----

@@ -259,6 +259,25 @@ int ensure_smem(const void* fn, size_t bytes, uint64_t* device_mask) {
     return HOLO_OK;
 }
 
+int resident_ctas(const void* fn, int threads, size_t bytes, int* cache, int* ctas) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    int n = __atomic_load_n(cache + (dev & 63), __ATOMIC_ACQUIRE);
+    if (n <= 0) {
+        int per_sm = 0, sms = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, bytes)) != cudaSuccess)
+            return cuda_status(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_status(e, "cudaDeviceGetAttribute(SM count)");
+        if (per_sm < 1) return fail(HOLO_ECUDA, "a kernel of %d threads and %zu bytes fits no SM", threads, bytes);
+        n = per_sm * sms;
+        __atomic_store_n(cache + (dev & 63), n, __ATOMIC_RELEASE);
+    }
+    *ctas = n;
+    return HOLO_OK;
+}
+
 }  // namespace holo
 
 // ================================================================== C ABI ====

@@ -110,5 +110,9 @@ holo_graph* make_holo_graph(cudaGraph_t graph, cudaGraphExec_t exec, int device,
 
 // Sets the dynamic shared-memory limit of kernel `fn` on the current device once.
 int ensure_smem(const void* fn, size_t bytes, uint64_t* device_mask);
+// *ctas = how many CTAs of kernel `fn` (threads, dynamic shared memory `bytes`) the current
+// device holds at once (CTAs per SM x SMs), found once per device and kept in cache[64]
+// (zero-initialised by the caller).
+int resident_ctas(const void* fn, int threads, size_t bytes, int* cache, int* ctas);
 
 }  // namespace holo

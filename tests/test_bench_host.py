@@ -68,6 +68,7 @@ def test_traffic_record_round_trip(bench, tmp_path, monkeypatch):
     traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 12)
     assert traffic == 4.4e7
     assert bench.measured_instructions("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 12) == 3.7e7
+    assert rec["per_launch"] == 12
     # another tile variant or pairs per launch than the capture's: no traffic
     traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 1, 0>", 12)
     assert traffic is None and "capture is of" in why
@@ -79,6 +80,26 @@ def test_traffic_record_round_trip(bench, tmp_path, monkeypatch):
     out.write_text(json.dumps(data))
     traffic, why = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 12)
     assert traffic is None and "changed" in why
+
+
+def test_traffic_record_of_a_one_dimensional_grid(bench, tmp_path, monkeypatch):
+    # the column IDFT launched as one CTA per resident slot: its pairs per launch are those
+    # of the row pass in the same capture
+    csv_path = tmp_path / "t.csv"
+    ci = "void holo::k_ospr_col_ifft<1024, 0>(holo::OsprArgs)"
+    row = "void holo::k_ospr_row<1024, 0, 1, 0>(holo::OsprArgs)"
+    _ncu_csv(csv_path, [(ci, "(152, 1, 1)", "dram__bytes_read.sum", "4,000,000"),
+                        (ci, "(152, 1, 1)", "dram__bytes_write.sum", "40,000,000"),
+                        (row, "(256, 12, 1)", "dram__bytes_read.sum", "100,000,000"),
+                        (row, "(256, 12, 1)", "dram__bytes_write.sum", "40,000,000")])
+    out = tmp_path / "traffic.json"
+    bench.record_traffic(str(csv_path), "ncu ...", str(out))
+    data = json.loads(out.read_text())
+    assert data["ospr_col_ifft"]["per_launch"] == 12 and data["ospr_row"]["per_launch"] == 12
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(out))
+    traffic, _ = bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 12)
+    assert traffic == 4.4e7
+    assert bench.measured_traffic("ospr_col_ifft", "k_ospr_col_ifft<1024, 0>", 8)[0] is None
 
 
 def test_launch_signatures(bench):
