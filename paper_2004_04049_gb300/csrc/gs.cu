@@ -101,10 +101,15 @@ template <int NC, int V>
 constexpr size_t gs_col_smem() {
     return sizeof(float2) * (256 + size_t(GsColCfg<NC, V>::LPC) * gs_col_stride<NC, V>());
 }
-// the row pass looks up the quantised codes in a 16-way replicated table (conflict-free)
+// The row pass looks up one quantised code per pixel in a 4-way replicated table (8 KiB;
+// lane l reads copy l mod 4, so a half-warp's 16 lookups meet about two-way bank conflicts).
+// Every 128-thread CTA loads the table for its two rows: 16 copies (32 KiB, conflict-free)
+// cost more in loads than they saved (1024^2 row pass 14.4 against 12.4 us; 8 targets of
+// 1024^2 62.9 k against 69.2 k iterations/s).
+constexpr int kGsRowCopies = 4;
 template <int NR, int V>
 constexpr size_t gs_row_smem() {
-    return sizeof(float2) * (kCsSmemEntries + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
+    return sizeof(float2) * (cs_smem_entries<kGsRowCopies>() + size_t(GsRowCfg<NR, V>::LPR) * line_stride(NR, GsRowCfg<NR, V>::R));
 }
 
 // Line FFT of a GS column pass (LPC lines of T threads, lane-consecutive columns)
@@ -282,8 +287,8 @@ k_gs_row(GsArgs a0) {
     const GsArgs a = gs_target(a0, blockIdx.y);
     extern __shared__ float2 sm[];
     float2* cs = sm;
-    float2* lines = sm + kCsSmemEntries;
-    load_cs_table(cs, a.cs256);
+    float2* lines = sm + cs_smem_entries<kGsRowCopies>();
+    load_cs_table<kGsRowCopies>(cs, a.cs256);
     pdl_wait();
     __syncthreads();
     const int line = threadIdx.x / T, t = threadIdx.x % T;
@@ -293,7 +298,7 @@ k_gs_row(GsArgs a0) {
 #pragma unroll
     for (int e = 0; e < R; ++e) v[e] = z[t + T * e];
     gs_row_line_fft<NR, V, +1>(v, lines, line, t, a);
-    gs_quantise_row<R, T, FRESNEL, kCsCopies>(v, a, cs, r, t);
+    gs_quantise_row<R, T, FRESNEL, kGsRowCopies>(v, a, cs, r, t);
     gs_row_line_fft<NR, V, -1>(v, lines, line, t, a);
     pdl_trigger();
 #pragma unroll
