@@ -501,7 +501,7 @@ int gs_state_phase(const float* d_state, int H, int W, float* d_phase, holo_stre
  * passes and the row pass each have variants 0..2 for line lengths 512..2048 (variant 0
  * only for other lengths; other values fall back to 0). Every variant computes the same
  * values up to float32 rounding order. Defaults are the fastest measured on GB300
- * (1024: column 0, row 1; 2048: column 1, row 2). gs_tuning_set with a negative variant
+ * (1024: column 0, row 1; 2048: column 1, row 1). gs_tuning_set with a negative variant
  * restores the defaults of the shape. Host-only calls; HOLO_EINVAL outside -1..2.
  */
 int gs_tuning_set(int H, int W, int col_variant, int row_variant);

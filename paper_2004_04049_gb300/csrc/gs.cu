@@ -371,7 +371,7 @@ static GsTiles gs_tiles(int H, int W) {
     }
     GsTiles t;
     t.col_v = H == 2048 ? 1 : 0;
-    t.row_v = W == 1024 ? 1 : (W == 2048 ? 2 : 0);
+    t.row_v = (W == 1024 || W == 2048) ? 1 : 0;
     return t;
 }
 

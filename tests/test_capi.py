@@ -142,7 +142,7 @@ def test_tuning_set_get_host_only(lib):
 
 def test_gs_tuning_host_only(lib):
     assert holo.gs_tuning_get(1024, 1024) == {"col_variant": 0, "row_variant": 1}
-    assert holo.gs_tuning_get(2048, 2048) == {"col_variant": 1, "row_variant": 2}
+    assert holo.gs_tuning_get(2048, 2048) == {"col_variant": 1, "row_variant": 1}
     holo.gs_tuning_set(256, 1024, 2, 2)   # 256-point columns have one variant
     try:
         assert holo.gs_tuning_get(256, 1024) == {"col_variant": 0, "row_variant": 2}

@@ -28,7 +28,8 @@ def _init_state(T, L, seed):
 
 @pytest.mark.parametrize("H,W,levels,kind", [(64, 64, 256, "blob"), (256, 256, 256, "noise"),
                                              (128, 512, 256, "blob"), (256, 128, 2, "blob"),
-                                             (1024, 1024, 256, "blob"), (64, 4096, 256, "noise"),
+                                             (1024, 1024, 256, "blob"), (1024, 2048, 256, "noise"),
+                                             (64, 4096, 256, "noise"),
                                              (4096, 64, 4, "blob")])
 def test_single_iteration_parity(cuda, H, W, levels, kind):
     _single_iteration(cuda, H, W, levels, kind)
